@@ -1,0 +1,191 @@
+"""FP64 CPU oracle for the level-blocked matrix-power kernel.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``; never by the library.  It shares
+no code with the CUDA path.  The arithmetic lives in ``mpk_oracle.c`` (plain
+sequential C, FP64, compiled with ``-ffp-contract=off``); this module builds it
+with gcc and wraps it with ctypes, converting numpy arrays only.
+
+Functions and the passages of the paper they restate:
+  spmv, mpk            Sec. 3.1, Fig. 1 (baseline MPK: pm back-to-back SpMVs)
+  bfs_levels           Sec. 4.1, Eq. 3 (+ restart rule for disconnected graphs)
+  level_perm           Sec. 4.1 (level-consecutive renumbering), Fig. 3e level_ptr
+  permute_csr          Sec. 4.1 footnote (symmetric permutation P A P^T)
+  level_groups         Sec. 4.2.1, Eq. 5 (greedy level groups)
+  lp_order             Sec. 4.2, Fig. 5 (diagonal traversal of the Lp diagram)
+  lb_mpk               Sec. 4.2, Fig. 5 run sequentially (levels or level groups)
+  gershgorin           spectral interval used for the Chebyshev scaling (Sec. 7)
+  cheb_coeffs_schroedinger, cheb   Sec. 7, Eq. 7-9
+
+Every function here is pinned by ``tests/test_oracle_*.py`` against closed
+forms, dense brute force, the paper's worked examples and invariants.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpk_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile mpk_oracle.c into oracle/_build/liboracle.so (gcc, FP64, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+            i32, f64 = C.c_int32, C.c_double
+            lib.oracle_spmv_rows.argtypes = [i32p, i32p, f64p, i32, f64p, f64p, i32, i32]
+            lib.oracle_mpk.argtypes = [i32, i32p, i32p, f64p, i32, i32, f64p, f64p]
+            lib.oracle_bfs_levels.argtypes = [i32, i32p, i32p, i32, i32, i32p]
+            lib.oracle_bfs_levels.restype = i32
+            lib.oracle_level_perm.argtypes = [i32, i32p, i32, i32p, i32p, i32p]
+            lib.oracle_permute_csr.argtypes = [i32, i32p, i32p, f64p, i32p, i32p, i32p, i32p, f64p]
+            lib.oracle_level_groups.argtypes = [i32, f64p, i32, f64, f64, i32p]
+            lib.oracle_level_groups.restype = i32
+            lib.oracle_lp_order.argtypes = [i32, i32, i32p, i32p]
+            lib.oracle_lp_order.restype = C.c_int64
+            lib.oracle_lb_mpk.argtypes = [i32, i32p, i32p, f64p, i32, i32p, i32, i32, f64p, f64p]
+            lib.oracle_gershgorin.argtypes = [i32, i32p, i32p, f64p, C.POINTER(f64), C.POINTER(f64)]
+            lib.oracle_cheb_coeffs_schroedinger.argtypes = [i32, f64, f64, f64, f64p]
+            lib.oracle_cheb.argtypes = [i32, i32p, i32p, f64p, f64, f64, i32, f64p, f64p, f64p]
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def spmv(A, x):
+    """y = A x (Fig. 1); x shape (n,) or (n, nrhs)."""
+    return mpk(A, x, 1)[0]
+
+
+def mpk(A, x, pm):
+    """Baseline MPK (Sec. 3.1): returns Y with Y[k-1] = A^k x, k = 1..pm."""
+    lib = _load()
+    x = _f64(x)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    Y = np.empty((pm,) + x.shape, dtype=np.float64)
+    lib.oracle_mpk(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), pm, nrhs, x, Y)
+    return Y
+
+
+def bfs_levels(A, root=0, symmetrize=False):
+    """Eq. 3 levels: returns (level[n] int32, nlevels)."""
+    lib = _load()
+    level = np.empty(A.n, dtype=np.int32)
+    L = lib.oracle_bfs_levels(A.n, _i32(A.rowptr), _i32(A.col), int(root), int(bool(symmetrize)), level)
+    return level, int(L)
+
+
+def level_perm(level, nlevels):
+    """Level-consecutive renumbering: returns (perm, iperm, level_ptr)."""
+    lib = _load()
+    n = level.shape[0]
+    perm = np.empty(n, dtype=np.int32)
+    iperm = np.empty(n, dtype=np.int32)
+    level_ptr = np.empty(nlevels + 1, dtype=np.int32)
+    lib.oracle_level_perm(n, _i32(level), nlevels, perm, iperm, level_ptr)
+    return perm, iperm, level_ptr
+
+
+def permute_csr(A, perm, iperm):
+    """P A P^T with each row's columns ascending; returns a CSR of the same class."""
+    lib = _load()
+    prow = np.empty(A.n + 1, dtype=np.int32)
+    pcol = np.empty(A.nnz, dtype=np.int32)
+    pval = np.empty(A.nnz, dtype=np.float64)
+    lib.oracle_permute_csr(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), _i32(perm), _i32(iperm),
+                           prow, pcol, pval)
+    return type(A)(A.n, prow, pcol, pval, name=A.name + "-perm")
+
+
+def level_groups(level_weight, pm, f, C_bytes):
+    """Eq. 5 greedy groups: returns group_ptr (level indices), length G+1."""
+    lib = _load()
+    w = _f64(level_weight)
+    gp = np.empty(w.shape[0] + 1, dtype=np.int32)
+    G = lib.oracle_level_groups(w.shape[0], w, int(pm), float(f), float(C_bytes), gp)
+    return gp[:G + 1].copy()
+
+
+def lp_order(nlevels, pm):
+    """Fig. 5 execution order: arrays (i, p) of the L_m * pm nodes, step 0 first."""
+    lib = _load()
+    cap = max(1, nlevels * pm)
+    ni = np.empty(cap, dtype=np.int32)
+    npw = np.empty(cap, dtype=np.int32)
+    s = lib.oracle_lp_order(int(nlevels), int(pm), ni, npw)
+    return ni[:s].copy(), npw[:s].copy()
+
+
+def lb_mpk(Aperm, unit_ptr, x, pm, fill=np.nan):
+    """Fig. 5 run sequentially over units (levels or level groups) of an
+    already permuted matrix; Y starts filled with `fill` so that a read of a
+    not-yet-computed entry shows up in the result."""
+    lib = _load()
+    x = _f64(x)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    Y = np.full((pm,) + x.shape, fill, dtype=np.float64)
+    up = _i32(unit_ptr)
+    lib.oracle_lb_mpk(Aperm.n, _i32(Aperm.rowptr), _i32(Aperm.col), _f64(Aperm.val),
+                      up.shape[0] - 1, up, pm, nrhs, x, Y)
+    return Y
+
+
+def gershgorin(A):
+    lib = _load()
+    lo, hi = C.c_double(), C.c_double()
+    lib.oracle_gershgorin(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def cheb_coeffs_schroedinger(M, c, r, dt):
+    """Complex coefficients (M+1,) of exp(-i H dt) in T_k((H-c)/r)."""
+    lib = _load()
+    out = np.empty(2 * (M + 1), dtype=np.float64)
+    lib.oracle_cheb_coeffs_schroedinger(int(M), float(c), float(r), float(dt), out)
+    return out[0::2] + 1j * out[1::2]
+
+
+def cheb(A, coef, c, r, x):
+    """y = sum_k coef_k T_k((A-c)/r) x for complex x (Eq. 7-9), FP64."""
+    lib = _load()
+    coef = np.asarray(coef, dtype=np.complex128)
+    M = coef.shape[0] - 1
+    xi = np.empty((A.n, 2), dtype=np.float64)
+    xi[:, 0] = np.real(x)
+    xi[:, 1] = np.imag(x)
+    ci = np.empty(2 * (M + 1), dtype=np.float64)
+    ci[0::2] = coef.real
+    ci[1::2] = coef.imag
+    y = np.empty((A.n, 2), dtype=np.float64)
+    lib.oracle_cheb(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), float(c), float(r), int(M), ci, xi, y)
+    return y[:, 0] + 1j * y[:, 1]

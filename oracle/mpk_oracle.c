@@ -1,0 +1,303 @@
+/*
+ * FP64 CPU oracle for the level-blocked matrix-power kernel (MPK).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path links, loads or
+ * calls this file; only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code, header or table with the CUDA
+ * library.  Every routine is a plain sequential restatement of a definition
+ * of the paper (Alappat et al., "Level-based Blocking for Sparse Matrices:
+ * Sparse Matrix-Power-Vector Multiplication"), cited per routine.
+ *
+ * Compiled with -O2 -ffp-contract=off so that every product and sum is a
+ * separately rounded IEEE binary64 operation, in the stored column order.
+ *
+ * Matrices are CRS with int32 row pointers and column indices (Sec. 3.1,
+ * Fig. 1).  Block vectors are row-major n x nrhs.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+int oracle_abi_version(void) { return 1; }
+
+/* ------------------------------------------------------------------ SpMV
+ * Fig. 1 (Sec. 3.1): out[row] = sum over the stored entries of `row` of
+ * val[idx] * in[col[idx]], for rows row_s..row_e inclusive, in stored order.
+ */
+void oracle_spmv_rows(const int32_t *rowptr, const int32_t *col, const double *val,
+                      int32_t nrhs, const double *in, double *out,
+                      int32_t row_s, int32_t row_e)
+{
+    for (int32_t row = row_s; row <= row_e; row++) {
+        for (int32_t c = 0; c < nrhs; c++) {
+            double tmp = 0.0;
+            for (int32_t idx = rowptr[row]; idx < rowptr[row + 1]; idx++)
+                tmp += val[idx] * in[(int64_t)col[idx] * nrhs + c];
+            out[(int64_t)row * nrhs + c] = tmp;
+        }
+    }
+}
+
+/* Baseline MPK (Sec. 3.1, Fig. 1): y_0 = x, y_p = A y_{p-1} for p = 1..pm.
+ * Y holds pm blocks of n*nrhs doubles, block p-1 = y_p. */
+void oracle_mpk(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                int32_t pm, int32_t nrhs, const double *x, double *Y)
+{
+    const int64_t blk = (int64_t)n * nrhs;
+    for (int32_t p = 1; p <= pm; p++) {
+        const double *in = (p == 1) ? x : Y + (int64_t)(p - 2) * blk;
+        if (n > 0)
+            oracle_spmv_rows(rowptr, col, val, nrhs, in, Y + (int64_t)(p - 1) * blk, 0, n - 1);
+    }
+}
+
+/* ------------------------------------------------------------------ levels
+ * Eq. 3 (Sec. 4.1): L(0) = {root}; L(i) = vertices in the neighbourhood of
+ * L(i-1) that carry no level yet.  Computed with a FIFO breadth-first search:
+ * a vertex's level is its hop distance from the root.
+ *
+ * Readings where the paper is silent:
+ *  - neighbourhood = stored pattern of A, plus that of A^T when `symmetrize`
+ *    is set (the paper restricts itself to symmetric patterns, Sec. 4);
+ *  - when the queue empties while vertices remain unvisited (a disconnected
+ *    graph), the lowest-numbered unvisited vertex starts a new component at
+ *    the next level number.
+ * Returns the number of levels L_m; level[v] receives v's level.
+ */
+int32_t oracle_bfs_levels(int32_t n, const int32_t *rowptr, const int32_t *col,
+                          int32_t root, int32_t symmetrize, int32_t *level)
+{
+    if (n <= 0) return 0;
+    int32_t *trp = NULL, *tcol = NULL;
+    if (symmetrize) {             /* CRS of the transposed pattern */
+        int64_t nnz = rowptr[n];
+        trp = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+        tcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+        for (int64_t e = 0; e < nnz; e++) trp[col[e] + 1]++;
+        for (int32_t v = 0; v < n; v++) trp[v + 1] += trp[v];
+        int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        memcpy(fill, trp, sizeof(int32_t) * (size_t)n);
+        for (int32_t u = 0; u < n; u++)
+            for (int32_t e = rowptr[u]; e < rowptr[u + 1]; e++) tcol[fill[col[e]]++] = u;
+        free(fill);
+    }
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t v = 0; v < n; v++) level[v] = -1;
+    int32_t head = 0, tail = 0, maxlevel = -1, next_unvisited = 0;
+    int32_t start = (root >= 0 && root < n) ? root : 0;
+    for (;;) {
+        level[start] = maxlevel + 1;
+        queue[tail++] = start;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            if (level[u] > maxlevel) maxlevel = level[u];
+            for (int32_t e = rowptr[u]; e < rowptr[u + 1]; e++) {
+                int32_t v = col[e];
+                if (level[v] < 0) { level[v] = level[u] + 1; queue[tail++] = v; }
+            }
+            if (symmetrize)
+                for (int32_t e = trp[u]; e < trp[u + 1]; e++) {
+                    int32_t v = tcol[e];
+                    if (level[v] < 0) { level[v] = level[u] + 1; queue[tail++] = v; }
+                }
+        }
+        while (next_unvisited < n && level[next_unvisited] >= 0) next_unvisited++;
+        if (next_unvisited == n) break;
+        start = next_unvisited;
+    }
+    free(queue); free(trp); free(tcol);
+    return maxlevel + 1;
+}
+
+/* Sec. 4.1: renumber so that the vertices of L(i-1) precede those of L(i)
+ * and each level is consecutive.  Reading: inside a level, ascending
+ * original index (a stable counting sort by level).
+ * perm[new] = old, iperm[old] = new, level_ptr[i] = first new index of L(i)
+ * (Fig. 3e), level_ptr[nlevels] = n. */
+void oracle_level_perm(int32_t n, const int32_t *level, int32_t nlevels,
+                       int32_t *perm, int32_t *iperm, int32_t *level_ptr)
+{
+    for (int32_t i = 0; i <= nlevels; i++) level_ptr[i] = 0;
+    for (int32_t v = 0; v < n; v++) level_ptr[level[v] + 1]++;
+    for (int32_t i = 0; i < nlevels; i++) level_ptr[i + 1] += level_ptr[i];
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nlevels > 0 ? nlevels : 1));
+    for (int32_t i = 0; i < nlevels; i++) pos[i] = level_ptr[i];
+    for (int32_t v = 0; v < n; v++) {
+        int32_t r = pos[level[v]]++;
+        perm[r] = v;
+        iperm[v] = r;
+    }
+    free(pos);
+}
+
+/* Symmetric permutation P A P^T (Sec. 4.1 footnote): new row r is old row
+ * perm[r], each column c becomes iperm[c]; entries of a row are put in
+ * ascending new-column order (stable for equal columns).  Output arrays
+ * are caller-allocated with n+1 / nnz entries. */
+void oracle_permute_csr(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                        const int32_t *perm, const int32_t *iperm,
+                        int32_t *prow, int32_t *pcol, double *pval)
+{
+    prow[0] = 0;
+    for (int32_t r = 0; r < n; r++) {
+        int32_t o = perm[r];
+        int32_t len = rowptr[o + 1] - rowptr[o];
+        int32_t base = prow[r];
+        prow[r + 1] = base + len;
+        for (int32_t j = 0; j < len; j++) {            /* insertion sort */
+            int32_t c = iperm[col[rowptr[o] + j]];
+            double a = val[rowptr[o] + j];
+            int32_t k = base + j;
+            while (k > base && pcol[k - 1] > c) { pcol[k] = pcol[k - 1]; pval[k] = pval[k - 1]; k--; }
+            pcol[k] = c; pval[k] = a;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ groups
+ * Eq. 5 (Sec. 4.2.1): starting at the first level not yet grouped, add
+ * consecutive levels to the group while (pm+1) * weight(T) < f * C holds,
+ * where weight(T) is the sum of the member levels' weights (the paper uses
+ * Nnz(T) * 12 bytes).  A level that violates the bound on its own forms a
+ * group by itself.  group_ptr[g] = first level of T(g); returns the group
+ * count G (group_ptr[G] = nlevels). */
+int32_t oracle_level_groups(int32_t nlevels, const double *level_weight, int32_t pm,
+                            double f, double C, int32_t *group_ptr)
+{
+    int32_t G = 0, start = 0;
+    const double budget = f * C;
+    while (start < nlevels) {
+        double acc = level_weight[start];
+        int32_t end = start + 1;
+        while (end < nlevels && (double)(pm + 1) * (acc + level_weight[end]) < budget) {
+            acc += level_weight[end];
+            end++;
+        }
+        group_ptr[G++] = start;
+        start = end;
+    }
+    group_ptr[G] = nlevels;
+    return G;
+}
+
+/* ------------------------------------------------------------------ Lp order
+ * Fig. 5 (Sec. 4.2): diagonals d = i + p ascending from 1 to L_m + pm - 1;
+ * inside a diagonal, p ascending from max(1, d - L_m + 1) to min(d, pm);
+ * node (i, p) with i = d - p.  Writes the nodes in execution order (step 0
+ * first) into node_i / node_p; returns the number of nodes (L_m * pm). */
+int64_t oracle_lp_order(int32_t nlevels, int32_t pm, int32_t *node_i, int32_t *node_p)
+{
+    int64_t s = 0;
+    for (int32_t d = 1; d <= nlevels + pm - 1; d++) {
+        int32_t p_start = (d - nlevels + 1 > 1) ? d - nlevels + 1 : 1;
+        int32_t p_end = (d < pm) ? d : pm;
+        for (int32_t p = p_start; p <= p_end; p++) {
+            node_i[s] = d - p;
+            node_p[s] = p;
+            s++;
+        }
+    }
+    return s;
+}
+
+/* Level-blocked MPK (Fig. 5) run sequentially on an already permuted
+ * matrix: every node (i, p) applies the SpMV of Fig. 1 to the rows of unit i
+ * (unit_ptr[i] .. unit_ptr[i+1]-1) reading y_{p-1}.  With unit_ptr =
+ * level_ptr this is the basic LB MPK; with the rows of level groups it is
+ * the LB+LG traversal of Sec. 4.2.1 (Fig. 7b).  Y must hold pm blocks. */
+void oracle_lb_mpk(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   int32_t nunits, const int32_t *unit_ptr, int32_t pm, int32_t nrhs,
+                   const double *x, double *Y)
+{
+    const int64_t blk = (int64_t)n * nrhs;
+    for (int32_t d = 1; d <= nunits + pm - 1; d++) {
+        int32_t p_start = (d - nunits + 1 > 1) ? d - nunits + 1 : 1;
+        int32_t p_end = (d < pm) ? d : pm;
+        for (int32_t p = p_start; p <= p_end; p++) {
+            int32_t i = d - p;
+            const double *in = (p == 1) ? x : Y + (int64_t)(p - 2) * blk;
+            if (unit_ptr[i + 1] > unit_ptr[i])
+                oracle_spmv_rows(rowptr, col, val, nrhs, in, Y + (int64_t)(p - 1) * blk,
+                                 unit_ptr[i], unit_ptr[i + 1] - 1);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ Chebyshev
+ * Gershgorin interval of A: [min_i (a_ii - sum_{j!=i} |a_ij|),
+ * max_i (a_ii + sum_{j!=i} |a_ij|)].  Reading of the spectral scaling the
+ * paper leaves unstated (Sec. 7): centre c = (hi+lo)/2, half-width r = (hi-lo)/2. */
+void oracle_gershgorin(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                       double *lo, double *hi)
+{
+    double l = INFINITY, h = -INFINITY;
+    for (int32_t i = 0; i < n; i++) {
+        double d = 0.0, s = 0.0;
+        for (int32_t e = rowptr[i]; e < rowptr[i + 1]; e++) {
+            if (col[e] == i) d += val[e]; else s += fabs(val[e]);
+        }
+        if (d - s < l) l = d - s;
+        if (d + s > h) h = d + s;
+    }
+    *lo = l; *hi = h;
+}
+
+/* Schroedinger propagator coefficients (hbar = 1): with H = c + r*Ahat,
+ * exp(-i H dt) = exp(-i c dt) [ J_0(r dt) T_0(Ahat) + 2 sum_{k>=1} (-i)^k J_k(r dt) T_k(Ahat) ]
+ * (Jacobi-Anger expansion; the Bessel-function coefficients of Sec. 7).
+ * coef holds M+1 complex numbers, interleaved (re, im). */
+void oracle_cheb_coeffs_schroedinger(int32_t M, double c, double r, double dt, double *coef)
+{
+    double ph_re = cos(c * dt), ph_im = -sin(c * dt);   /* exp(-i c dt) */
+    for (int32_t k = 0; k <= M; k++) {
+        double a = (k == 0 ? 1.0 : 2.0) * jn(k, r * dt);
+        double mi_re, mi_im;                               /* (-i)^k */
+        switch (k & 3) {
+        case 0: mi_re = 1.0;  mi_im = 0.0;  break;
+        case 1: mi_re = 0.0;  mi_im = -1.0; break;
+        case 2: mi_re = -1.0; mi_im = 0.0;  break;
+        default: mi_re = 0.0; mi_im = 1.0;  break;
+        }
+        double t_re = a * mi_re, t_im = a * mi_im;
+        coef[2 * k]     = ph_re * t_re - ph_im * t_im;
+        coef[2 * k + 1] = ph_re * t_im + ph_im * t_re;
+    }
+}
+
+/* Chebyshev time propagation (Sec. 7, Eq. 7-9) for a real matrix A and a
+ * complex vector x (interleaved re, im; row-major n x 2):
+ *   Ahat = (A - c I) / r,  v_0 = x,  v_1 = Ahat v_0,
+ *   v_{k+1} = 2 Ahat v_k - v_{k-1},  y = sum_{k=0}^{M} coef_k v_k,
+ * with complex coef (interleaved).  All arithmetic in FP64. */
+void oracle_cheb(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                 double c, double r, int32_t M, const double *coef, const double *x, double *y)
+{
+    const int64_t len = (int64_t)n * 2;
+    double *vprev = (double *)malloc(sizeof(double) * (size_t)(len > 0 ? len : 1));
+    double *vcur  = (double *)malloc(sizeof(double) * (size_t)(len > 0 ? len : 1));
+    double *av    = (double *)malloc(sizeof(double) * (size_t)(len > 0 ? len : 1));
+    memcpy(vprev, x, sizeof(double) * (size_t)len);
+    for (int64_t i = 0; i < n; i++) {              /* y = coef_0 * v_0 */
+        double vr = x[2 * i], vi = x[2 * i + 1];
+        y[2 * i]     = coef[0] * vr - coef[1] * vi;
+        y[2 * i + 1] = coef[0] * vi + coef[1] * vr;
+    }
+    for (int32_t k = 1; k <= M; k++) {
+        const double *src = (k == 1) ? vprev : vcur;
+        if (n > 0) oracle_spmv_rows(rowptr, col, val, 2, src, av, 0, n - 1);
+        for (int64_t i = 0; i < len; i++) {
+            double ah = (av[i] - c * src[i]) / r;  /* Ahat v */
+            double vnew = (k == 1) ? ah : 2.0 * ah - vprev[i];
+            if (k > 1) vprev[i] = vcur[i];
+            vcur[i] = vnew;
+        }
+        const double cr = coef[2 * k], ci = coef[2 * k + 1];
+        for (int64_t i = 0; i < n; i++) {
+            double vr = vcur[2 * i], vi = vcur[2 * i + 1];
+            y[2 * i]     += cr * vr - ci * vi;
+            y[2 * i + 1] += cr * vi + ci * vr;
+        }
+    }
+    free(vprev); free(vcur); free(av);
+}
