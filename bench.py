@@ -1,0 +1,337 @@
+"""Benchmark of the level-blocked matrix-power kernel on one GB300 (or N replicas).
+
+Default workload: 3D 7-point Laplacian on a 160^3 grid (N = 4,096,000,
+nnz = 28,518,400), FP64, p = 8.  One step = one level-blocked MPK
+(y_k = A^k x, k = 1..8) in a single persistent wavefront launch, vectors in
+the plan's level order (the paper times in permuted space).  The plan
+(levels, groups, packing) is built once before timing and reported apart,
+as the paper reports preprocessing apart.
+
+The JSON line carries: GFLOP/s (2 nnz p / t) for the whole job, the same
+metric end to end through the public API with host buffers, the baseline of
+p back-to-back SpMVs on the same GPU and the speedup over it, the FP32 form,
+the roofline of the dominant kernel, the CPU oracle timed on the host and the
+SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config NAME]
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); the FP64 MPK is ALU bound
+
+CONFIGS = {
+    # name: (generator, p, precision, description)
+    "laplace3d-160-p8-f64": ("laplace3d", 160, 8, "f64", "3D 7-point Laplacian 160^3, p=8, FP64"),
+    "laplace3d-160-p8-f32": ("laplace3d", 160, 8, "f32", "3D 7-point Laplacian 160^3, p=8, FP32"),
+    "laplace2d-64-p4-f64": ("laplace2d", 64, 4, "f64", "2D 5-point Laplacian 64^2, p=4, FP64"),
+}
+DEFAULT = "laplace3d-160-p8-f64"
+
+
+def make_matrix(kind, size):
+    import mpk_inputs as mi
+    return getattr(mi, kind)(size)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks (NVML, read only)
+class ClockSampler:
+    """Samples the SM clock and the clock-event reasons through NVML while
+    running (read-only queries; nothing is set)."""
+
+    HW_SLOWDOWN, SW_THERMAL, HW_THERMAL, SW_POWER_CAP = 0x8, 0x20, 0x40, 0x4
+
+    def __init__(self, index=0, period_s=0.002):
+        self.period = period_s
+        self.samples, self.reasons = [], 0
+        self.max_mhz = None
+        self.ok = False
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.nvml.nvmlDeviceGetHandleByIndex_v2(index, ctypes.byref(self.h)) != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.ok = True
+        except OSError:
+            pass
+
+    def _one(self):
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+            self.samples.append(clk.value)
+        fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(self.nvml, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        if fn(self.h, ctypes.byref(rs)) == 0:
+            self.reasons |= rs.value
+
+    def __enter__(self):
+        self._stop = threading.Event()
+        if self.ok:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._one()
+            time.sleep(self.period)
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self.ok:
+            self._t.join()
+            self._one()
+
+    def summary(self):
+        names = []
+        if self.reasons & self.HW_SLOWDOWN:
+            names.append("hw_slowdown")
+        if self.reasons & self.HW_THERMAL:
+            names.append("hw_thermal_slowdown")
+        if self.reasons & self.SW_THERMAL:
+            names.append("sw_thermal_slowdown")
+        if self.reasons & self.SW_POWER_CAP:
+            names.append("sw_power_cap")
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "reasons": names, "samples": len(self.samples),
+                "source": "nvml" if self.ok else "unavailable"}
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def time_oracle(A, x, p, budget_s=12.0):
+    """The FP64 CPU oracle (sequential C, one core) on the full matrix,
+    repeated until `budget_s` of work; returns (GFLOP/s, reps, seconds)."""
+    import oracle
+    oracle.mpk(A, x, 1)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.mpk(A, x, p)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return 2.0 * A.nnz * p * reps / el / 1e9, reps, el
+
+
+def dist_setup(n_gpus):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return rank, ws, dist
+    return 0, 1, None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    kind, size, p, prec, desc = CONFIGS[args.config]
+    cfg = {"workload": desc, "n": None, "nnz": None, "p": p, "prec": prec,
+           "io": "level order (permuted space)", "l2": "inputs larger than L2 (matrix > 129 MB)",
+           "data": "synthetic"}
+
+    if args.impl == "reference":
+        return run_reference(args, kind, size, p, cfg)
+
+    import torch
+    import mpk_inputs as mi
+    import paper_2205_01598_gb300 as mpk
+    rank, ws, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    mpk.build()
+    mpk.load()
+
+    A = make_matrix(kind, size)
+    cfg["n"], cfg["nnz"] = A.n, A.nnz
+    flops = 2.0 * A.nnz * p
+    rp, cl, va = mpk.csr_to_device(A)
+    plan = mpk.mpk_plan(rp, cl, va, p, prec=prec)
+    info = mpk.mpk_plan_info(plan)
+    perm = mpk.mpk_plan_perm(plan)[0]
+    vdt = torch.float64 if prec == "f64" else torch.float32
+    x_host = mi.random_vector(A.n, 1234)
+    x = torch.from_numpy(x_host).to(vdt).cuda()[perm.long()].contiguous()
+    Y = torch.empty(p, A.n, dtype=vdt, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            e0.record(st)
+            for _ in range(steps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # headline: level-blocked MPK, one persistent launch per step
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    ms = timed(lambda: mpk.mpk_run(plan, x, Y, permuted=True, asynchronous=True), args.steps, args.warmup, sampler)
+    mpk.mpk_run(plan, x, Y, permuted=True)   # synchronous call: surfaces any device-side error
+    value = ws * flops / (ms * 1e-3) / 1e9
+
+    # baseline: p back-to-back SpMVs over the same packed matrix, same GPU
+    ms_base = timed(lambda: mpk.mpk_baseline_run(plan, x, Y, permuted=True, asynchronous=True),
+                    args.steps, args.warmup)
+
+    # end to end through the public API: host x -> device, mpk_run in the
+    # caller's numbering (gather / scatter inside), Y -> host
+    xh = torch.from_numpy(x_host).to(vdt).pin_memory()
+    Yh = torch.empty(p, A.n, dtype=vdt).pin_memory()
+    xd = torch.empty(A.n, dtype=vdt, device="cuda")
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        mpk.mpk_run(plan, xd, Y, asynchronous=True)
+        Yh.copy_(Y, non_blocking=True)
+
+    ms_e2e = timed(e2e_step, max(3, min(args.steps, 20)), 2)
+    value_e2e = ws * flops / (ms_e2e * 1e-3) / 1e9
+
+    peaks, peak_src = load_peaks()
+    # the FP64 path is bound by FP64 arithmetic (1 FMA per stored entry and power)
+    if prec == "f64":
+        achieved = flops / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "nominal FP64 rate of the profiling recipe"}
+    else:
+        vb = 4
+        alg_bytes = info["nnz"] * (vb + 4) + (A.n + 1) * 4 + A.n * vb * (1 + p)
+        achieved = alg_bytes / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        gf, reps, el = time_oracle(A, x_host, p)
+        cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"full matrix, p={p}, {reps} MPK runs in {el:.1f} s (sequential FP64 C)"}
+
+    clocks = sampler.summary()
+    out = {
+        "metric": "MPK GFLOP/s (2*nnz*p/t)",
+        "value": round(value, 3),
+        "unit": "GFLOP/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32"}[prec],
+        "data": "synthetic",
+        "config": cfg,
+        "speedup_vs_pxspmv": round(ms_base / ms, 4),
+        "baseline_pxspmv": {"ms_per_step": round(ms_base, 5), "value": round(ws * flops / (ms_base * 1e-3) / 1e9, 3),
+                            "gpu_launches_per_step": p},
+        "e2e": {"value": round(value_e2e, 3), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": A.n * x.element_size(),
+                "d2h_bytes_per_step": p * A.n * Y.element_size(), "ms_per_step": round(ms_e2e, 4)},
+        "gpu_launches": args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "plan": {"ms": round(info["plan_ms"], 2), "spmv_equiv": round(info["plan_ms"] / (ms_base / p), 1),
+                 "levels": info["n_levels"], "groups": info["n_groups"], "tiles": info["n_tiles"],
+                 "tile_rows": info["tile_rows"], "grid_ctas": info["grid_ctas"],
+                 "cache_bytes": info["cache_bytes"], "matrix_bytes": info["matrix_bytes"]},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def run_reference(args, kind, size, p, cfg):
+    """Reference arm: the FP64 CPU oracle (sequential C) on the host cores,
+    rank 0 only; each step is one full MPK of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import mpk_inputs as mi
+    import oracle
+    oracle.build()
+    A = make_matrix(kind, size)
+    cfg["n"], cfg["nnz"] = A.n, A.nnz
+    x = mi.random_vector(A.n, 1234)
+    steps, warm = max(1, min(args.steps, 10)), max(0, min(args.warmup, 1))
+    for _ in range(warm):
+        oracle.mpk(A, x, p)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.mpk(A, x, p)
+    el = time.perf_counter() - t0
+    value = 2.0 * A.nnz * p * steps / el / 1e9
+    out = {"impl": "reference", "metric": "MPK GFLOP/s (2*nnz*p/t)", "value": round(value, 4), "unit": "GFLOP/s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": warm,
+           "ms_per_step": round(el / steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{steps} full MPK runs (p={p}) of the workload"},
+           "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

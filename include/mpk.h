@@ -1,0 +1,212 @@
+/*
+ * mpk.h - C ABI of the GB300 level-blocked matrix-power kernel library.
+ *
+ * The library computes the matrix-power kernel (MPK)
+ *     y_0 = x,   y_k = A y_{k-1},   k = 1..p
+ * for a square sparse matrix A (Sec. 3, first paragraph), using level-based
+ * blocking (Sec. 4): a breadth-first search on the graph of A gives levels
+ * (Eq. 3), rows are renumbered level by level, consecutive levels are
+ * aggregated into level groups that fit the cache (Eq. 5), and a diagonal
+ * wavefront over (level group, power) pairs (Fig. 5, with the point-to-point
+ * conditions of Sec. 4.3) lets each slice of A be reused from on-chip memory
+ * for several powers instead of being read from HBM p times.  It also runs
+ * the Chebyshev time propagation built on the MPK (Sec. 7, Eq. 7-9).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an mpk_status (0 = MPK_OK, negative = error) and
+ *    never aborts the process.  mpk_strerror() names a status.
+ *  - All matrix and vector pointers are DEVICE pointers on the current CUDA
+ *    device unless a parameter says "host".  The caller owns them; the
+ *    library never frees them and does not keep them after the call returns
+ *    (mpk_plan copies what it needs).
+ *  - The library owns a plan and all device memory inside it; release it
+ *    with mpk_plan_destroy().
+ *  - Work is ordered on the stream given in mpk_opts.stream (a cudaStream_t;
+ *    NULL = the legacy default stream).  Calls that must report a
+ *    device-side error synchronise that stream unless MPK_ASYNC is given.
+ *  - Integers of the matrix are 32-bit (Fig. 1: int col[], rowPtr[]).
+ *  - A plan is not thread-safe: calls on one plan must not overlap in time
+ *    or on the GPU (they share the plan's dependency flags).
+ */
+#ifndef MPK_H
+#define MPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+    MPK_OK = 0,
+    MPK_ERR_INVALID = -1,     /* bad argument, or a malformed matrix          */
+    MPK_ERR_CUDA = -2,        /* a CUDA runtime call failed                   */
+    MPK_ERR_OOM = -3,         /* a device or host allocation failed           */
+    MPK_ERR_TIMEOUT = -4,     /* a device-side dependency wait hit its limit  */
+    MPK_ERR_UNSUPPORTED = -5  /* a valid request this build cannot serve      */
+} mpk_status;
+
+/* Storage / arithmetic precision of a plan.
+ *  MPK_F64         matrix values, vectors and sums in FP64.
+ *  MPK_F32         matrix values, vectors and sums in FP32.
+ *  MPK_F32_BF16VAL vectors and sums in FP32; diagonal entries kept in FP32,
+ *                  off-diagonal values stored as BF16 when every one of them
+ *                  is exactly representable in BF16 (else FP32; see
+ *                  mpk_plan_stats.val_bytes).                                */
+typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
+
+/* Flags of mpk_run / mpk_baseline_run / mpk_cheb. */
+#define MPK_IO_PERMUTED 1u  /* x and outputs are in the plan's level order   */
+#define MPK_ASYNC       2u  /* do not synchronise to read the device error word */
+
+/* A square sparse matrix in CRS form (Sec. 3.1, Fig. 1).  Device pointers,
+ * caller-owned.  rowptr[n+1] (rowptr[0] = 0, non-decreasing, rowptr[n] = nnz),
+ * col[nnz] in [0, n), val[nnz] FP64.  Column order inside a row is free.
+ * assume_symmetric != 0 promises a structurally symmetric pattern; with 0 the
+ * levels are computed on the pattern of A + A^T (Sec. 4 restricts the method
+ * to symmetric patterns; the MPK itself always multiplies by A).          */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t *rowptr;
+    const int32_t *col;
+    const double *val;
+    int32_t assume_symmetric;
+} mpk_csr;
+
+/* Planning options; initialise with mpk_opts_default().                  */
+typedef struct {
+    int32_t root;          /* BFS root vertex v_root (Sec. 4.1); default 0      */
+    double cache_bytes;    /* C of Eq. 5 in bytes; 0 = the device's L2 size     */
+    double safety_f;       /* f of Eq. 5; default 0.5 (Sec. 4.2.1)              */
+    int32_t prec;          /* mpk_prec                                          */
+    int32_t nrhs;          /* columns of the block vectors x, y_k (row-major)   */
+    int32_t tile_rows;     /* rows per work item, multiple of 32; 0 = automatic */
+    int32_t ctas_per_sm;   /* resident CTAs per SM of the wavefront; 0 = auto   */
+    double timeout_s;      /* limit of every device-side wait; 0 = 2 seconds   */
+    void *stream;          /* cudaStream_t for all work of this plan            */
+} mpk_opts;
+
+/* Summary of a plan (all host values).                                    */
+typedef struct {
+    int32_t n, p, nrhs, prec;
+    int64_t nnz;
+    int32_t n_levels;      /* L_m                                                */
+    int32_t n_groups;      /* number of level groups T(0..G-1)                   */
+    int32_t n_tiles;       /* work items per power                               */
+    int32_t max_level_rows;
+    int32_t tile_rows;
+    int32_t grid_ctas;     /* CTAs of the persistent wavefront launch            */
+    int32_t val_bytes;     /* bytes per stored off-diagonal value (8, 4 or 2)    */
+    int64_t packed_entries;/* stored entries incl. padding of the packed layout  */
+    int64_t matrix_bytes;  /* device bytes of the packed matrix (values+indices) */
+    int64_t device_bytes;  /* all device memory held by the plan                 */
+    double plan_ms;        /* wall time of mpk_plan                              */
+    double cache_bytes;    /* C actually used in Eq. 5                           */
+} mpk_plan_stats;
+
+typedef struct mpk_plan_s *mpk_plan_t;
+
+/* Fills *o with the defaults above.  MPK_ERR_INVALID if o is NULL.        */
+int mpk_opts_default(mpk_opts *o);
+
+/* Builds the level-blocked plan of A for powers 1..p (Sec. 4.5: the
+ * preprocessing takes the matrix, p_m and C and yields the permutation).
+ * On the GPU: validation, BFS levels (Eq. 3; when the search runs out of
+ * vertices the lowest-numbered unvisited vertex starts the next level),
+ * stable renumbering by (level, original index), the symmetric permutation
+ * P A P^T, greedy level groups (Eq. 5, weight = stored entries x bytes per
+ * entry of the chosen precision), the packed SELL-32 matrix and the
+ * dependency ranges of the wavefront.  1 <= p <= 255, 1 <= nrhs <= 64.
+ * Errors: MPK_ERR_INVALID (NULL pointers, n < 1, p or nrhs out of range,
+ * malformed CRS found on the device), MPK_ERR_OOM, MPK_ERR_CUDA.  On error
+ * *out is set to NULL and nothing is leaked.                              */
+int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out);
+
+/* Copies the plan summary to host memory *s.                              */
+int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s);
+
+/* Copies plan arrays to caller-allocated DEVICE buffers; any may be NULL.
+ *  perm[n]        perm[new] = old (Sec. 4.5: recovers the original order)
+ *  level_ptr[L+1] first new row of each level (Fig. 3e); level_ptr[L] = n
+ *  group_ptr[G+1] first level of each level group; group_ptr[G] = L
+ *  level[n]       Eq. 3 level of each ORIGINAL vertex                      */
+int mpk_plan_perm(mpk_plan_t plan, int32_t *perm, int32_t *level_ptr, int32_t *group_ptr,
+                  int32_t *level);
+
+/* Level-blocked MPK (Sec. 4, Fig. 5 with level groups and point-to-point
+ * synchronisation): Y[k-1] = A^k x for k = 1..p in ONE persistent launch.
+ * x: n x nrhs row-major; Y: p consecutive blocks of n x nrhs.  Element type
+ * double for MPK_F64, float otherwise.  Without MPK_IO_PERMUTED, x and Y are
+ * in the caller's original numbering (the library gathers x and scatters Y
+ * through a plan-owned buffer); with it, both are in the plan's level order
+ * (new index r holds original vertex perm[r]), which is the fast path.
+ * x and Y must not overlap.  Errors: MPK_ERR_INVALID, MPK_ERR_CUDA,
+ * MPK_ERR_TIMEOUT (a wait exceeded opts.timeout_s; the outputs are then
+ * incomplete), MPK_ERR_OOM (first unpermuted run on a large matrix).      */
+int mpk_run(mpk_plan_t plan, const void *x, void *Y, uint32_t flags);
+
+/* Baseline MPK (Sec. 3.1, Fig. 1): p back-to-back SpMV launches over the
+ * same packed matrix, y_k = A y_{k-1}.  Same arguments and results as
+ * mpk_run; it is the comparator the level-blocked kernel is measured
+ * against.                                                                */
+int mpk_baseline_run(mpk_plan_t plan, const void *x, void *Y, uint32_t flags);
+
+/* Gershgorin interval [lo, hi] of A (host outputs), from the plan's matrix:
+ * lo = min_i (a_ii - sum_{j != i} |a_ij|), hi = max_i (a_ii + sum |a_ij|).
+ * Used for the spectral scaling Ahat = (A - c)/r, c = (hi+lo)/2,
+ * r = (hi-lo)/2, of the Chebyshev propagation (Sec. 7).                    */
+int mpk_gershgorin(mpk_plan_t plan, double *lo, double *hi);
+
+/* Host helper: the M+1 complex coefficients (interleaved re, im, HOST
+ * memory) of exp(-i H dt) = sum_k coef_k T_k((H - c)/r) for the Schroedinger
+ * equation (Sec. 7; Bessel-function coefficients, hbar = 1):
+ * coef_0 = e^{-i c dt} J_0(r dt), coef_k = 2 e^{-i c dt} (-i)^k J_k(r dt).  */
+int mpk_cheb_coeffs_schroedinger(int32_t M, double c, double r, double dt, double *coef);
+
+/* Chebyshev time propagation (Sec. 7, Eq. 7-9) with the level-blocked MPK:
+ *   Ahat = (A - c I)/r,  v_0 = x,  v_1 = Ahat v_0,  v_{k+1} = 2 Ahat v_k - v_{k-1},
+ *   y = sum_{k=0}^{M} coef_k v_k,
+ * where the M matrix applications run as ceil(M/p) wavefront sweeps of at
+ * most p powers each (Sec. 7: M split into batches of p_m).  The plan must
+ * have nrhs = 2: x and v_k are complex vectors stored as n x 2 (re, im) in
+ * the plan precision (double for MPK_F64, float otherwise); y is n x 2
+ * DOUBLE (the coefficient sum is accumulated in FP64).  coef: M+1 complex
+ * numbers, interleaved, HOST memory.  Flags as for mpk_run.  Errors as for
+ * mpk_run; MPK_ERR_INVALID if nrhs != 2, M < 1 or r == 0.                  */
+int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
+             const void *x, double *y, uint32_t flags);
+
+/* Reorders vectors between the caller's numbering and the plan's level
+ * order (Sec. 4.5: the permutation vector recovers the original order).
+ * src and dst: count blocks of n x nrhs elements of elem_bytes (4 or 8)
+ * each, not overlapping.  to_level != 0: dst[r] = src[perm[r]]; else
+ * dst[perm[r]] = src[r].                                                   */
+int mpk_permute_vectors(mpk_plan_t plan, const void *src, void *dst, int32_t count,
+                        int32_t elem_bytes, int32_t to_level);
+
+/* Releases the plan and all its device memory (after finishing its stream's
+ * work).  NULL is accepted.                                                */
+int mpk_plan_destroy(mpk_plan_t plan);
+
+/* Test hook for the bounded waits: the NEXT wavefront launch of this plan
+ * does not publish the completion of work item (tile, power), so the items
+ * that read it reach their wait limit (opts.timeout_s) and the call returns
+ * MPK_ERR_TIMEOUT with that node in mpk_plan_last_error; later launches are
+ * unaffected.  No fault, trap or unbounded wait is involved.  tile < 0
+ * cancels a pending drop.  MPK_ERR_INVALID for an item outside the plan.  */
+int mpk_plan_debug_drop_flag(mpk_plan_t plan, int32_t tile, int32_t power);
+
+/* Static description of a status code.                                     */
+const char *mpk_strerror(int status);
+
+/* Detail of the last device-side error of the plan (host outputs; any may be
+ * NULL): code (an mpk_status), the power k and the work item (tile) whose
+ * wait expired.                                                            */
+int mpk_plan_last_error(mpk_plan_t plan, int32_t *code, int32_t *power, int32_t *tile);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPK_H */

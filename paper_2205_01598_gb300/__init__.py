@@ -1,0 +1,289 @@
+"""Python binding of the GB300 level-blocked matrix-power kernel (MPK) library.
+
+Thin ctypes layer over the C ABI declared in ``include/mpk.h``: every function
+here has the name of the C entry point it calls and only marshals arguments
+(torch CUDA tensors -> device pointers, the current torch stream -> the
+plan's cudaStream_t).  All computation runs in the CUDA kernels of
+``csrc/``; there is no CPU fallback.  If the shared library has not been
+built, every call raises ``RuntimeError``.
+
+Build it in-tree with :func:`build` (nvcc, sm_103a).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libmpk.so")
+HEADER = os.path.join(_ROOT, "include", "mpk.h")
+SOURCES = ["mpk_plan.cu", "mpk_exec.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
+
+MPK_OK, MPK_ERR_INVALID, MPK_ERR_CUDA, MPK_ERR_OOM, MPK_ERR_TIMEOUT, MPK_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+MPK_F64, MPK_F32, MPK_F32_BF16VAL = 0, 1, 2
+MPK_IO_PERMUTED, MPK_ASYNC = 1, 2
+PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL}
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a into _build/libmpk.so (in parallel)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = [os.path.join(_CSRC, s) for s in SOURCES] + [os.path.join(_CSRC, "mpk_internal.cuh"), HEADER]
+    newest = max(os.path.getmtime(d) for d in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc] + NVCC_FLAGS + ["-c", os.path.join(_CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.check_call(cmd)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class mpk_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("assume_symmetric", C.c_int32)]
+
+
+class mpk_opts(C.Structure):
+    _fields_ = [("root", C.c_int32), ("cache_bytes", C.c_double), ("safety_f", C.c_double),
+                ("prec", C.c_int32), ("nrhs", C.c_int32), ("tile_rows", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+
+
+class mpk_plan_stats(C.Structure):
+    _fields_ = [("n", C.c_int32), ("p", C.c_int32), ("nrhs", C.c_int32), ("prec", C.c_int32),
+                ("nnz", C.c_int64), ("n_levels", C.c_int32), ("n_groups", C.c_int32),
+                ("n_tiles", C.c_int32), ("max_level_rows", C.c_int32), ("tile_rows", C.c_int32),
+                ("grid_ctas", C.c_int32), ("val_bytes", C.c_int32), ("packed_entries", C.c_int64),
+                ("matrix_bytes", C.c_int64), ("device_bytes", C.c_int64), ("plan_ms", C.c_double),
+                ("cache_bytes", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load the shared library (no CUDA call is made by loading it)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"the MPK CUDA library is not built ({path}); run "
+                               "paper_2205_01598_gb300.build() first")
+        lib = C.CDLL(path)
+        vp, i32, i64, u32, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+        sig = {
+            "mpk_opts_default": ([C.POINTER(mpk_opts)], C.c_int),
+            "mpk_plan": ([C.POINTER(mpk_csr), i32, C.POINTER(mpk_opts), C.POINTER(vp)], C.c_int),
+            "mpk_plan_info": ([vp, C.POINTER(mpk_plan_stats)], C.c_int),
+            "mpk_plan_perm": ([vp, vp, vp, vp, vp], C.c_int),
+            "mpk_run": ([vp, vp, vp, u32], C.c_int),
+            "mpk_baseline_run": ([vp, vp, vp, u32], C.c_int),
+            "mpk_gershgorin": ([vp, C.POINTER(f64), C.POINTER(f64)], C.c_int),
+            "mpk_cheb_coeffs_schroedinger": ([i32, f64, f64, f64, vp], C.c_int),
+            "mpk_cheb": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
+            "mpk_permute_vectors": ([vp, vp, vp, i32, i32, i32], C.c_int),
+            "mpk_plan_destroy": ([vp], C.c_int),
+            "mpk_strerror": ([C.c_int], C.c_char_p),
+            "mpk_plan_last_error": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
+            "mpk_plan_debug_drop_flag": ([vp, i32, i32], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+class MpkError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = load().mpk_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code})")
+
+
+def _check(code, where):
+    if code != MPK_OK:
+        raise MpkError(code, where)
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owner of an ``mpk_plan_t``; released by :func:`mpk_plan_destroy` or GC."""
+
+    def __init__(self, handle, p, nrhs, prec, n, stream):
+        self.handle = handle
+        self.p, self.nrhs, self.prec, self.n = p, nrhs, prec, n
+        self.stream = stream
+
+    @property
+    def vec_dtype(self):
+        import torch
+        return torch.float64 if self.prec == MPK_F64 else torch.float32
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mpk_plan_destroy(self.handle)
+            self.handle = None
+
+
+def mpk_opts_default():
+    o = mpk_opts()
+    _check(load().mpk_opts_default(C.byref(o)), "mpk_opts_default")
+    return o
+
+
+def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=0.0, safety_f=0.5,
+             prec="f64", nrhs=1, tile_rows=0, ctas_per_sm=0, timeout_s=2.0, stream=None) -> Plan:
+    """Level-blocked plan of the CRS matrix (rowptr, col: int32 CUDA tensors,
+    val: float64 CUDA tensor) for powers 1..p (mpk_plan)."""
+    import torch
+    lib = load()
+    assert rowptr.dtype == torch.int32 and col.dtype == torch.int32 and val.dtype == torch.float64
+    A = mpk_csr(n=rowptr.numel() - 1, nnz=col.numel(), rowptr=_ptr(rowptr), col=_ptr(col), val=_ptr(val),
+                assume_symmetric=int(bool(assume_symmetric)))
+    o = mpk_opts_default()
+    o.root, o.cache_bytes, o.safety_f = int(root), float(cache_bytes), float(safety_f)
+    o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    o.nrhs, o.tile_rows, o.ctas_per_sm, o.timeout_s = int(nrhs), int(tile_rows), int(ctas_per_sm), float(timeout_s)
+    o.stream = _stream(stream)
+    h = C.c_void_p()
+    _check(lib.mpk_plan(C.byref(A), int(p), C.byref(o), C.byref(h)), "mpk_plan")
+    return Plan(h, int(p), int(nrhs), o.prec, A.n, stream)
+
+
+def mpk_plan_info(plan: Plan) -> dict:
+    s = mpk_plan_stats()
+    _check(load().mpk_plan_info(plan.handle, C.byref(s)), "mpk_plan_info")
+    return {name: getattr(s, name) for name, _ in mpk_plan_stats._fields_}
+
+
+def mpk_plan_perm(plan: Plan):
+    """(perm, level_ptr, group_ptr, level) as int32 CUDA tensors."""
+    import torch
+    info = mpk_plan_info(plan)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    perm = torch.empty(plan.n, dtype=torch.int32, device=dev)
+    lp = torch.empty(info["n_levels"] + 1, dtype=torch.int32, device=dev)
+    gp = torch.empty(info["n_groups"] + 1, dtype=torch.int32, device=dev)
+    lev = torch.empty(plan.n, dtype=torch.int32, device=dev)
+    _check(load().mpk_plan_perm(plan.handle, _ptr(perm), _ptr(lp), _ptr(gp), _ptr(lev)), "mpk_plan_perm")
+    return perm, lp, gp, lev
+
+
+def _flags(permuted, asynchronous):
+    return (MPK_IO_PERMUTED if permuted else 0) | (MPK_ASYNC if asynchronous else 0)
+
+
+def mpk_run(plan: Plan, x, Y, permuted=False, asynchronous=False):
+    """Y[k-1] = A^k x, k = 1..p, level-blocked (mpk_run)."""
+    _check(load().mpk_run(plan.handle, _ptr(x), _ptr(Y), _flags(permuted, asynchronous)), "mpk_run")
+
+
+def mpk_baseline_run(plan: Plan, x, Y, permuted=False, asynchronous=False):
+    """Y[k-1] = A^k x by p back-to-back SpMV launches (mpk_baseline_run)."""
+    _check(load().mpk_baseline_run(plan.handle, _ptr(x), _ptr(Y), _flags(permuted, asynchronous)),
+           "mpk_baseline_run")
+
+
+def mpk_gershgorin(plan: Plan):
+    lo, hi = C.c_double(), C.c_double()
+    _check(load().mpk_gershgorin(plan.handle, C.byref(lo), C.byref(hi)), "mpk_gershgorin")
+    return lo.value, hi.value
+
+
+def mpk_cheb_coeffs_schroedinger(M, c, r, dt) -> np.ndarray:
+    out = np.empty(2 * (M + 1), dtype=np.float64)
+    _check(load().mpk_cheb_coeffs_schroedinger(int(M), float(c), float(r), float(dt),
+                                               out.ctypes.data_as(C.c_void_p)), "mpk_cheb_coeffs_schroedinger")
+    return out[0::2] + 1j * out[1::2]
+
+
+def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False):
+    """y = sum_k coef_k T_k((A - c)/r) x (mpk_cheb); x: (n, 2) plan precision,
+    y: (n, 2) float64 CUDA tensors; coef: complex host array of length M+1."""
+    coef = np.asarray(coef, dtype=np.complex128)
+    ci = np.empty(2 * coef.shape[0], dtype=np.float64)
+    ci[0::2], ci[1::2] = coef.real, coef.imag
+    _check(load().mpk_cheb(plan.handle, ci.ctypes.data_as(C.c_void_p), coef.shape[0] - 1, float(c), float(r),
+                           _ptr(x), _ptr(y), _flags(permuted, asynchronous)), "mpk_cheb")
+
+
+def mpk_permute_vectors(plan: Plan, src, dst, count, to_level):
+    _check(load().mpk_permute_vectors(plan.handle, _ptr(src), _ptr(dst), int(count), src.element_size(),
+                                      int(bool(to_level))), "mpk_permute_vectors")
+
+
+def mpk_plan_last_error(plan: Plan):
+    code, k, t = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().mpk_plan_last_error(plan.handle, C.byref(code), C.byref(k), C.byref(t)), "mpk_plan_last_error")
+    return code.value, k.value, t.value
+
+
+def mpk_plan_debug_drop_flag(plan: Plan, tile, power):
+    """Test hook: the next wavefront launch does not publish item (tile, power)."""
+    _check(load().mpk_plan_debug_drop_flag(plan.handle, int(tile), int(power)), "mpk_plan_debug_drop_flag")
+
+
+def mpk_plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(load().mpk_plan_destroy(plan.handle), "mpk_plan_destroy")
+        plan.handle = None
+
+
+def mpk_strerror(code: int) -> str:
+    return load().mpk_strerror(int(code)).decode()
+
+
+def csr_to_device(A, device="cuda"):
+    """Copies a host CRS (objects with rowptr/col/val numpy arrays) to CUDA tensors."""
+    import torch
+    return (torch.from_numpy(np.ascontiguousarray(A.rowptr, dtype=np.int32)).to(device),
+            torch.from_numpy(np.ascontiguousarray(A.col, dtype=np.int32)).to(device),
+            torch.from_numpy(np.ascontiguousarray(A.val, dtype=np.float64)).to(device))

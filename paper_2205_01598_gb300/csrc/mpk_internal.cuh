@@ -1,0 +1,171 @@
+// Internal declarations of the GB300 level-blocked MPK library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <new>
+#include <vector>
+
+#include "mpk.h"
+
+namespace mpk {
+
+constexpr int kChunk = 32;         // rows per SELL chunk = one warp, one row per lane
+constexpr int kMaxP = 255;         // powers are packed in 8 bits of a work item
+constexpr int kMaxNrhs = 64;
+constexpr int kWaveThreads = 256;  // threads of one wavefront CTA
+
+// Control words of a plan (device int32 array).
+enum Ctl : int {
+    CTL_NEXT = 0,       // next work item to hand out
+    CTL_FINISHED = 1,   // CTAs that left the dispatch loop in this launch
+    CTL_EPOCH = 2,      // epoch of the last completed launch (flags hold epochs)
+    CTL_ABORT = 3,      // set when a wait expired: every CTA stops taking work
+    CTL_ERR = 4,        // mpk_status of the first device-side error (0 = none)
+    CTL_ERR_K = 5,      // power of the node whose wait expired
+    CTL_ERR_T = 6,      // tile of the node whose wait expired
+    CTL_WORDS = 8
+};
+
+struct Plan {
+    // sizes and options
+    int32_t n = 0, p = 0, nrhs = 1, prec = MPK_F64;
+    int64_t nnz = 0;
+    int32_t n_levels = 0, n_groups = 0, n_tiles = 0, n_chunks = 0;
+    int32_t tile_rows = 0, max_level_rows = 0;
+    int32_t grid_ctas = 0, ctas_per_sm = 0;
+    int32_t val_bytes = 8;
+    int32_t has_diag = 0;           // diagonal stored apart (BF16 values)
+    double cache_bytes = 0, safety_f = 0.5, timeout_s = 2.0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int64_t packed_entries = 0, device_bytes = 0;
+    double plan_ms = 0;
+    uint64_t launches = 0;
+    int32_t drop_tile = -1, drop_k = -1;   // one-shot test hook (mpk_plan_debug_drop_flag)
+
+    std::vector<int32_t> h_level_ptr, h_group_ptr;
+
+    // device arrays (plan-owned)
+    int32_t *d_perm = nullptr, *d_iperm = nullptr, *d_level = nullptr;
+    int32_t *d_level_ptr = nullptr, *d_group_ptr = nullptr;
+    int32_t *d_chunk_row = nullptr;    // n_chunks+1: first row of each chunk (sentinel n)
+    int64_t *d_chunk_off = nullptr;    // n_chunks+1: first packed entry of each chunk
+    int32_t *d_tile_chunk = nullptr;   // n_tiles+1: first chunk of each tile
+    int32_t *d_dep_lo = nullptr, *d_dep_hi = nullptr;  // n_tiles: tiles read at power k-1
+    int32_t *d_work = nullptr;         // p*n_tiles items, (tile << 8) | power
+    int32_t *d_pcol = nullptr;         // packed column indices, -1 = padding
+    void *d_pval = nullptr;            // packed values (double / float / bf16)
+    float *d_diag = nullptr;           // diagonal (only with has_diag)
+    double *d_gersh = nullptr;         // Gershgorin row bounds scratch (lazily)
+    uint32_t *d_flags = nullptr;       // (p+1)*n_tiles completion epochs
+    int32_t *d_ctl = nullptr;          // CTL_WORDS control words
+    void *d_io = nullptr;              // permuted copies for unpermuted I/O (lazily)
+    size_t io_bytes = 0;
+    void *d_cheb = nullptr;            // Chebyshev vector ring (lazily)
+    size_t cheb_bytes = 0;
+};
+
+// Parameters of the wavefront / baseline kernels.
+struct ExecArgs {
+    const int32_t *chunk_row;
+    const int64_t *chunk_off;
+    const int32_t *tile_chunk;
+    const int32_t *dep_lo, *dep_hi;
+    const int32_t *work;
+    const int32_t *pcol;
+    const void *pval;
+    const float *diag;
+    uint32_t *flags;
+    int32_t *ctl;
+    int32_t n_tiles, n_items, n_chunks, nrhs, p;
+    int64_t blk;            // elements of one vector block (n * nrhs)
+    const void *x;          // y_0
+    void *Y;                // p blocks
+    uint64_t timeout_ns;
+    int32_t drop_tile, drop_k;   // completion not published (test hook), -1 = none
+};
+
+// Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).
+struct ChebArgs {
+    ExecArgs e;
+    void *ring;             // 3 vector blocks (n x 2) cycling v_{k-2}, v_{k-1}, v_k
+    double *acc;            // n x 2 FP64 coefficient sum
+    const double *coef;     // device copy of all coefficients (interleaved complex)
+    double alpha, beta;     // Ahat v = alpha*(A v) + beta*v with alpha = 1/r, beta = -c/r
+    int32_t k0;             // powers already computed before this sweep
+};
+
+// ---------------------------------------------------------------- host helpers
+int cuda_status(cudaError_t e, const char *what, int line);
+#define MPK_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::mpk::cuda_status(_e, #call, __LINE__); \
+    } while (0)
+
+template <typename T>
+int dev_alloc(Plan *pl, T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *ptr = nullptr;
+        return e == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA;
+    }
+    if (pl) pl->device_bytes += (int64_t)(count * sizeof(T));
+    return MPK_OK;
+}
+
+// Exclusive scans used by the planner (device, on `st`); tmp is sized by the helper.
+int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st, int32_t *total);
+int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st, int64_t *total);
+
+// Execution entry points used across translation units.
+int launch_wavefront(Plan *pl, const void *x, void *Y, cudaStream_t st);
+int launch_baseline(Plan *pl, const void *x, void *Y, cudaStream_t st);
+int launch_cheb_sweep(Plan *pl, const ChebArgs &a, int32_t powers, cudaStream_t st);
+int read_device_error(Plan *pl, cudaStream_t st);
+int permute_vectors(Plan *pl, const void *src, void *dst, int32_t count, int32_t elem_bytes,
+                    int32_t to_level, cudaStream_t st);
+ExecArgs exec_args(const Plan *pl, const void *x, void *Y);
+int ensure_io(Plan *pl, size_t bytes);
+
+inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
+
+}  // namespace mpk
+
+struct mpk_plan_s {
+    mpk::Plan pl;
+};
+
+// ---------------------------------------------------------------- device helpers
+namespace mpk {
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ld_relaxed_s32(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+}  // namespace mpk

@@ -1,0 +1,905 @@
+// Plan construction of the level-blocked MPK: levels (Eq. 3), renumbering
+// (Sec. 4.1), level groups (Eq. 5), packed SELL-32 matrix and the
+// dependency ranges of the (level group, power) wavefront (Fig. 5, Sec. 4.3).
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstring>
+
+#include "mpk_internal.cuh"
+
+namespace mpk {
+
+int wave_occupancy(const Plan *pl, int *ctas_per_sm);   // mpk_exec.cu
+
+int cuda_status(cudaError_t e, const char *what, int line) {
+    (void)cudaGetLastError();
+    if (getenv("MPK_DEBUG")) fprintf(stderr, "mpk: %s failed at line %d: %s\n", what, line, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA;
+}
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// ---------------------------------------------------------------- scans
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *warp_sums, T *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        T s = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    T before = (w > 0 ? warp_sums[w - 1] : T(0)) + x - v;
+    if (total) *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+template <typename T>
+__global__ void k_scan_reduce(const T *in, int64_t n, T *sums) {
+    __shared__ T ws[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T s = 0;
+    for (int i = 0; i < kScanItems; i++)
+        if (base + i < n) s += in[base + i];
+    T tot;
+    block_exclusive_scan<T>(s, ws, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void k_scan_sums(T *sums, int64_t nb, T *grand) {   // one block, in place
+    __shared__ T ws[32];
+    T carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        int64_t i = b0 + threadIdx.x;
+        T v = i < nb ? sums[i] : T(0);
+        T tot;
+        T ex = block_exclusive_scan<T>(v, ws, &tot);
+        if (i < nb) sums[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+template <typename T>
+__global__ void k_scan_apply(const T *in, T *out, int64_t n, const T *sums) {
+    __shared__ T ws[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    T vals[kScanItems];
+    T s = 0;
+    for (int i = 0; i < kScanItems; i++) {
+        vals[i] = base + i < n ? in[base + i] : T(0);
+        s += vals[i];
+    }
+    T run = block_exclusive_scan<T>(s, ws, nullptr) + sums[blockIdx.x];
+    for (int i = 0; i < kScanItems; i++) {
+        if (base + i < n) out[base + i] = run;
+        run += vals[i];
+    }
+}
+
+template <typename T>
+int exclusive_scan(const T *in, T *out, int64_t n, cudaStream_t st, T *total) {
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb < 1) nb = 1;
+    T *sums = nullptr;
+    MPK_CUDA(cudaMallocAsync((void **)&sums, sizeof(T) * (size_t)(nb + 1), st));
+    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, n, sums);
+    k_scan_sums<T><<<1, 1024, 0, st>>>(sums, nb, sums + nb);
+    k_scan_apply<T><<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && total) e = cudaMemcpyAsync(total, sums + nb, sizeof(T), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && total) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(sums, st);
+    if (e != cudaSuccess) return cuda_status(e, "scan", __LINE__);
+    return MPK_OK;
+}
+
+// ---------------------------------------------------------------- validation
+__global__ void k_validate(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *col, int32_t *bad) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > n) return;
+    if (r == 0 && rp[0] != 0) atomicOr(bad, 1);
+    if (r == n) {
+        if ((int64_t)rp[n] != nnz) atomicOr(bad, 2);
+        return;
+    }
+    int32_t a = rp[r], b = rp[r + 1];
+    if (b < a || a < 0 || (int64_t)b > nnz) {
+        atomicOr(bad, 4);
+        return;
+    }
+    for (int32_t e = a; e < b; e++) {
+        int32_t c = col[e];
+        if (c < 0 || c >= n) {
+            atomicOr(bad, 8);
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- transpose pattern
+__global__ void k_count_cols(int64_t nnz, const int32_t *col, int32_t *cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[e]], 1);
+}
+__global__ void k_fill_transpose(int32_t n, const int32_t *rp, const int32_t *col, int32_t *fill, int32_t *tcol) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int32_t e = rp[r]; e < rp[r + 1]; e++) tcol[atomicAdd(&fill[col[e]], 1)] = r;
+}
+
+// ---------------------------------------------------------------- BFS (Eq. 3)
+struct BfsCtl {
+    unsigned bar_count, bar_gen;
+    int cnt[3];      // frontier sizes, rotating by level mod 3
+    int found[3];    // restart search results, rotating by search round mod 3
+    int nlevels;
+    int err;
+};
+
+// Grid-wide barrier of a cooperative launch with a bounded wait.
+__device__ bool grid_sync(BfsCtl *c, uint64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_relaxed_u32(&c->bar_gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&c->bar_gen, gen + 1);
+        } else {
+            uint64_t t0 = global_ns();
+            unsigned ns = 32;
+            while (ld_relaxed_u32(&c->bar_gen) == gen) {
+                if (ld_relaxed_s32(&c->err)) { ok = 0; break; }
+                if (global_ns() - t0 > timeout_ns) { atomicCAS(&c->err, 0, (int)MPK_ERR_TIMEOUT); ok = 0; break; }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        fence_acq_rel_gpu();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Level-synchronous top-down BFS over the pattern (and its transpose when
+// trp != null).  Levels are hop distances from the root; when a level comes
+// out empty while vertices remain, the lowest-numbered unvisited vertex
+// starts the next level.  level[] must be -1 on entry.
+__global__ void __launch_bounds__(512) k_bfs(int32_t n, const int32_t *rp, const int32_t *col,
+                                             const int32_t *trp, const int32_t *tcol, int32_t root,
+                                             int32_t *level, int32_t *queue, BfsCtl *c, uint64_t timeout_ns) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
+    if (gtid == 0) {
+        level[root] = 0;
+        queue[0] = root;
+        c->cnt[0] = 1;
+        c->found[0] = c->found[1] = c->found[2] = INT_MAX;
+    }
+    if (!grid_sync(c, timeout_ns)) return;
+    int32_t L = 0;
+    int64_t start = 0, cursor = 0;
+    int round = 0;
+    for (;;) {
+        int32_t size = ld_relaxed_s32(&c->cnt[L % 3]);
+        if (size == 0) {   // component finished: restart at the lowest unvisited vertex
+            int32_t f = INT_MAX;
+            for (;;) {
+                const int slot = round % 3;
+                if (gtid == 0) c->found[(round + 1) % 3] = INT_MAX;
+                int64_t idx = cursor + gtid;
+                if (idx < n && ld_relaxed_s32(&level[idx]) < 0) atomicMin(&c->found[slot], (int)idx);
+                if (!grid_sync(c, timeout_ns)) return;
+                f = ld_relaxed_s32(&c->found[slot]);
+                round++;
+                if (f != INT_MAX) break;
+                cursor += gsize;
+                if (cursor >= n) break;
+            }
+            if (f == INT_MAX) break;
+            cursor = f + 1;
+            if (gtid == 0) {
+                level[f] = L;
+                queue[start] = f;
+                c->cnt[L % 3] = 1;
+            }
+            if (!grid_sync(c, timeout_ns)) return;
+            size = 1;
+        }
+        if (gtid == 0) c->cnt[(L + 2) % 3] = 0;
+        int *next_cnt = &c->cnt[(L + 1) % 3];
+        const int64_t end = start + size;
+        for (int64_t base = start + gwarp * 32; base < end; base += nwarps * 32) {
+            int64_t i = base + lane;
+            bool valid = i < end;
+            int32_t u = valid ? queue[i] : 0;
+            int32_t a0 = 0, da = 0, t0 = 0, dt = 0;
+            if (valid) {
+                a0 = rp[u];
+                da = rp[u + 1] - a0;
+                if (trp) { t0 = trp[u]; dt = trp[u + 1] - t0; }
+            }
+            int32_t deg = da + dt;
+            int32_t maxdeg = __reduce_max_sync(0xffffffffu, (unsigned)deg);
+            for (int32_t j = 0; j < maxdeg; j++) {
+                bool disc = false;
+                int32_t v = 0;
+                if (j < deg) {
+                    v = j < da ? col[a0 + j] : tcol[t0 + (j - da)];
+                    if (ld_relaxed_s32(&level[v]) < 0) disc = atomicCAS(&level[v], -1, L + 1) == -1;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, disc);
+                if (m) {
+                    int leader = __ffs(m) - 1;
+                    int pos = 0;
+                    if (lane == leader) pos = atomicAdd(next_cnt, __popc(m));
+                    pos = __shfl_sync(0xffffffffu, pos, leader);
+                    if (disc) queue[end + pos + __popc(m & ((1u << lane) - 1u))] = v;
+                }
+            }
+        }
+        if (!grid_sync(c, timeout_ns)) return;
+        start = end;
+        L++;
+    }
+    if (gtid == 0) c->nlevels = L;
+}
+
+// ---------------------------------------------------------------- stable radix sort by level
+constexpr int kRsThreads = 256, kRsRounds = 16, kRsTile = kRsThreads * kRsRounds;
+
+__global__ void k_rs_hist(const int32_t *keys, int32_t n, int shift, int32_t *hist, int32_t nb) {
+    __shared__ int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+    for (int i = threadIdx.x; i < kRsTile; i += blockDim.x)
+        if (base + i < n) atomicAdd(&h[((uint32_t)keys[base + i] >> shift) & 255u], 1);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nb + blockIdx.x] = h[d];
+}
+
+// Stable scatter: items keep their input order inside each digit bucket.
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const int32_t *kin, const int32_t *vin, int32_t *kout,
+                                                           int32_t *vout, int32_t n, int shift,
+                                                           const int32_t *hscan, int32_t nb) {
+    __shared__ int wc[kRsThreads / 32][257];
+    __shared__ int base[256];
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int d = tid; d < 256; d += blockDim.x) base[d] = hscan[(int64_t)d * nb + blockIdx.x];
+    for (int r = 0; r < kRsRounds; r++) {
+        for (int i = tid; i < (kRsThreads / 32) * 257; i += blockDim.x) (&wc[0][0])[i] = 0;
+        __syncthreads();
+        int64_t i = (int64_t)blockIdx.x * kRsTile + r * kRsThreads + tid;
+        bool valid = i < n;
+        int32_t key = valid ? kin[i] : 0;
+        int d = valid ? (int)(((uint32_t)key >> shift) & 255u) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        if (rank == 0) wc[w][d] = __popc(peers);
+        __syncthreads();
+        if (tid < 256) {
+            int run = base[tid];
+            for (int ww = 0; ww < kRsThreads / 32; ww++) {
+                int t = wc[ww][tid];
+                wc[ww][tid] = run;
+                run += t;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            int pos = wc[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = vin ? vin[i] : (int32_t)i;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_inverse_perm(int32_t n, const int32_t *perm, int32_t *iperm) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) iperm[perm[r]] = r;
+}
+
+__global__ void k_level_ptr(int32_t n, const int32_t *sorted_level, int32_t *level_ptr, int32_t nlevels) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (r == 0) {
+        level_ptr[0] = 0;
+        level_ptr[nlevels] = n;
+    } else if (sorted_level[r] != sorted_level[r - 1]) {
+        level_ptr[sorted_level[r]] = r;   // levels are consecutive integers
+    }
+}
+
+// ---------------------------------------------------------------- permuted CRS
+__global__ void k_perm_len(int32_t n, const int32_t *rp, const int32_t *perm, int32_t *len) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) len[r] = rp[perm[r] + 1] - rp[perm[r]];
+}
+
+// Row r of P A P^T = old row perm[r], columns renumbered through iperm and
+// put in ascending order (insertion sort; rows are short).
+__global__ void k_perm_fill(int32_t n, const int32_t *rp, const int32_t *col, const double *val,
+                            const int32_t *perm, const int32_t *iperm, const int32_t *prow,
+                            int32_t *pcol, double *pval) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int32_t o = perm[r], a = rp[o], len = rp[o + 1] - a, base = prow[r];
+    for (int32_t j = 0; j < len; j++) {
+        int32_t c = iperm[col[a + j]];
+        double v = val[a + j];
+        int32_t k = base + j;
+        while (k > base && pcol[k - 1] > c) {
+            pcol[k] = pcol[k - 1];
+            pval[k] = pval[k - 1];
+            k--;
+        }
+        pcol[k] = c;
+        pval[k] = v;
+    }
+}
+
+__global__ void k_level_nnz(int32_t nlevels, const int32_t *level_ptr, const int32_t *prow, int64_t *lnnz) {
+    int32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nlevels) lnnz[l] = (int64_t)prow[level_ptr[l + 1]] - prow[level_ptr[l]];
+}
+
+// 1 if every off-diagonal value is exactly a bfloat16
+__global__ void k_bf16_exact(int32_t n, const int32_t *prow, const int32_t *pcol, const double *pval, int32_t *not_exact) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
+        if (pcol[e] == r) continue;
+        double v = pval[e];
+        float f = (float)v;
+        __nv_bfloat16 b = __float2bfloat16_rn(f);
+        if ((double)__bfloat162float(b) != v) { atomicOr(not_exact, 1); return; }
+    }
+}
+
+// ---------------------------------------------------------------- packing
+// Entries of row r that go into the SELL arrays (all of them, or all but the
+// diagonal when the diagonal is stored apart).
+__device__ __forceinline__ int32_t packed_len(int32_t r, const int32_t *prow, const int32_t *pcol, int split_diag) {
+    int32_t len = prow[r + 1] - prow[r];
+    if (split_diag)
+        for (int32_t e = prow[r]; e < prow[r + 1]; e++) len -= (pcol[e] == r);
+    return len;
+}
+
+__global__ void k_chunk_width(int32_t n_chunks, const int32_t *chunk_row, const int32_t *prow, const int32_t *pcol,
+                              int split_diag, int64_t *cw) {
+    int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
+    int32_t w = 0;
+    for (int32_t r = chunk_row[c]; r < chunk_row[c + 1]; r++) w = max(w, packed_len(r, prow, pcol, split_diag));
+    cw[c] = (int64_t)w * kChunk;
+}
+
+template <typename MT>
+__device__ __forceinline__ MT cvt_val(double v);
+template <> __device__ __forceinline__ double cvt_val<double>(double v) { return v; }
+template <> __device__ __forceinline__ float cvt_val<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt_val<__nv_bfloat16>(double v) {
+    return __float2bfloat16_rn((float)v);
+}
+
+// Column-major SELL-32: entry j of lane l of chunk c sits at off[c] + 32*j + l.
+template <typename MT>
+__global__ void k_pack(int32_t n_chunks, const int32_t *chunk_row, const int64_t *chunk_off, const int32_t *prow,
+                       const int32_t *pcol, const double *pval, int split_diag, int32_t *scol, MT *sval, float *diag) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t c = (int32_t)(g / kChunk);
+    int lane = (int)(g % kChunk);
+    if (c >= n_chunks) return;
+    int64_t off = chunk_off[c] + lane;
+    int32_t w = (int32_t)((chunk_off[c + 1] - chunk_off[c]) / kChunk);
+    int32_t r = chunk_row[c] + lane;
+    int32_t j = 0;
+    if (r < chunk_row[c + 1]) {
+        double d = 0.0;
+        for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
+            if (split_diag && pcol[e] == r) { d += pval[e]; continue; }
+            scol[off + (int64_t)j * kChunk] = pcol[e];
+            sval[off + (int64_t)j * kChunk] = cvt_val<MT>(pval[e]);
+            j++;
+        }
+        if (split_diag) diag[r] = (float)d;
+    }
+    for (; j < w; j++) {
+        scol[off + (int64_t)j * kChunk] = -1;
+        sval[off + (int64_t)j * kChunk] = cvt_val<MT>(0.0);
+    }
+}
+
+// ---------------------------------------------------------------- dependency ranges
+__global__ void k_tile_of_row(int32_t n_tiles, const int32_t *tile_row, int32_t *tor) {
+    int32_t t = blockIdx.x;
+    if (t >= n_tiles) return;
+    for (int32_t r = tile_row[t] + threadIdx.x; r < tile_row[t + 1]; r += blockDim.x) tor[r] = t;
+}
+
+// Tile t at power k reads y_{k-1} on the columns of its rows; the tiles that
+// hold those rows form a contiguous range (Eq. 4: columns of a level lie in
+// the neighbouring levels).  For a non-symmetric pattern the range is closed
+// under transposition so that "t reads u" implies "u reads t".
+__global__ void k_deps(int32_t n, const int32_t *prow, const int32_t *pcol, const int32_t *tor, int symmetric,
+                       int32_t *lo, int32_t *hi) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int32_t t = tor[r], mn = t, mx = t;
+    for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
+        int32_t u = tor[pcol[e]];
+        mn = min(mn, u);
+        mx = max(mx, u);
+        if (!symmetric) {
+            atomicMin(&lo[u], t);
+            atomicMax(&hi[u], t);
+        }
+    }
+    atomicMin(&lo[t], mn);
+    atomicMax(&hi[t], mx);
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// Temporary device buffers of the planner, freed on scope exit.
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    int alloc(T **p, size_t count) {
+        int rc = dev_alloc<T>(nullptr, p, count);
+        if (rc == MPK_OK) ptrs.push_back(*p);
+        return rc;
+    }
+};
+
+#define MPK_TRY(x)                 \
+    do {                           \
+        int _rc = (x);             \
+        if (_rc != MPK_OK) return _rc; \
+    } while (0)
+
+void free_plan(Plan *pl) {
+    void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
+                  pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
+                  pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+}
+
+int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
+    const auto t_start = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)o->stream;
+    pl->stream = st;
+    pl->n = A->n;
+    pl->nnz = A->nnz;
+    pl->p = p;
+    pl->nrhs = o->nrhs;
+    pl->prec = o->prec;
+    pl->safety_f = o->safety_f;
+    pl->timeout_s = o->timeout_s > 0 ? o->timeout_s : 2.0;
+    const uint64_t timeout_ns = (uint64_t)(pl->timeout_s * 1e9);
+    MPK_CUDA(cudaGetDevice(&pl->device));
+    cudaDeviceProp prop;
+    MPK_CUDA(cudaGetDeviceProperties(&prop, pl->device));
+    pl->num_sms = prop.multiProcessorCount;
+    pl->cache_bytes = o->cache_bytes > 0 ? o->cache_bytes : (double)prop.l2CacheSize;
+    const int32_t n = A->n;
+    const int64_t nnz = A->nnz;
+    Scratch S;
+
+    // 1. validation of the CRS arrays on the device
+    int32_t *d_bad;
+    MPK_TRY(S.alloc(&d_bad, 4));
+    MPK_CUDA(cudaMemsetAsync(d_bad, 0, 4 * sizeof(int32_t), st));
+    k_validate<<<blocks_for((int64_t)n + 1, 256), 256, 0, st>>>(n, nnz, A->rowptr, A->col, d_bad);
+    int32_t h_bad = 0;
+    MPK_CUDA(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    if (h_bad) return MPK_ERR_INVALID;
+
+    // 2. transposed pattern when symmetry is not promised
+    int32_t *d_trp = nullptr, *d_tcol = nullptr;
+    if (!A->assume_symmetric) {
+        int32_t *cnt;
+        MPK_TRY(S.alloc(&cnt, (size_t)n + 1));
+        MPK_TRY(S.alloc(&d_trp, (size_t)n + 1));
+        MPK_TRY(S.alloc(&d_tcol, (size_t)nnz));
+        MPK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)n + 1), st));
+        k_count_cols<<<std::min<unsigned>(blocks_for(nnz, 256), 4096), 256, 0, st>>>(nnz, A->col, cnt);
+        MPK_TRY(exclusive_scan<int32_t>(cnt, d_trp, (int64_t)n + 1, st, nullptr));
+        MPK_CUDA(cudaMemcpyAsync(cnt, d_trp, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        k_fill_transpose<<<blocks_for(n, 256), 256, 0, st>>>(n, A->rowptr, A->col, cnt, d_tcol);
+    }
+
+    // 3. BFS levels (Eq. 3), one cooperative launch
+    int32_t *d_queue;
+    BfsCtl *d_bc;
+    MPK_TRY(dev_alloc(pl, &pl->d_level, (size_t)n));
+    MPK_TRY(S.alloc(&d_queue, (size_t)n));
+    MPK_TRY(S.alloc(&d_bc, 1));
+    MPK_CUDA(cudaMemsetAsync(pl->d_level, 0xff, sizeof(int32_t) * (size_t)n, st));
+    MPK_CUDA(cudaMemsetAsync(d_bc, 0, sizeof(BfsCtl), st));
+    {
+        int occ = 0;
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, 512, 0));
+        if (occ < 1) return MPK_ERR_CUDA;
+        int grid = pl->num_sms * std::min(occ, 2);
+        int32_t root = (o->root >= 0 && o->root < n) ? o->root : 0;
+        const int32_t *rp = A->rowptr, *cl = A->col;
+        int32_t *lvl = pl->d_level;
+        uint64_t tns = timeout_ns;
+        void *args[] = {(void *)&n, (void *)&rp, (void *)&cl, (void *)&d_trp, (void *)&d_tcol, (void *)&root,
+                        (void *)&lvl, (void *)&d_queue, (void *)&d_bc, (void *)&tns};
+        MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(grid), dim3(512), args, 0, st));
+    }
+    BfsCtl h_bc;
+    MPK_CUDA(cudaMemcpyAsync(&h_bc, d_bc, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    if (h_bc.err) return h_bc.err;
+    const int32_t L = h_bc.nlevels;
+    if (L < 1 || L > n) return MPK_ERR_CUDA;
+    pl->n_levels = L;
+
+    // 4. stable renumbering by (level, original index): LSD radix sort on levels
+    int32_t *kA, *kB, *vA, *vB, *hist;
+    const int32_t nb = (int32_t)((n + kRsTile - 1) / kRsTile);
+    MPK_TRY(S.alloc(&kA, (size_t)n));
+    MPK_TRY(S.alloc(&kB, (size_t)n));
+    MPK_TRY(S.alloc(&vA, (size_t)n));
+    MPK_TRY(S.alloc(&vB, (size_t)n));
+    MPK_TRY(S.alloc(&hist, (size_t)256 * nb));
+    MPK_CUDA(cudaMemcpyAsync(kA, pl->d_level, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    int passes = 0;
+    for (uint32_t m = (uint32_t)(L - 1); m; m >>= 8) passes++;
+    if (passes == 0) passes = 1;
+    bool first = true;
+    for (int ps = 0; ps < passes; ps++) {
+        k_rs_hist<<<nb, kRsThreads, 0, st>>>(kA, n, 8 * ps, hist, nb);
+        MPK_TRY(exclusive_scan<int32_t>(hist, hist, (int64_t)256 * nb, st, nullptr));
+        k_rs_scatter<<<nb, kRsThreads, 0, st>>>(kA, first ? nullptr : vA, kB, vB, n, 8 * ps, hist, nb);
+        first = false;
+        std::swap(kA, kB);
+        std::swap(vA, vB);
+    }
+    MPK_TRY(dev_alloc(pl, &pl->d_perm, (size_t)n));
+    MPK_TRY(dev_alloc(pl, &pl->d_iperm, (size_t)n));
+    MPK_TRY(dev_alloc(pl, &pl->d_level_ptr, (size_t)L + 1));
+    MPK_CUDA(cudaMemcpyAsync(pl->d_perm, vA, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    k_inverse_perm<<<blocks_for(n, 256), 256, 0, st>>>(n, pl->d_perm, pl->d_iperm);
+    k_level_ptr<<<blocks_for(n, 256), 256, 0, st>>>(n, kA, pl->d_level_ptr, L);
+
+    // 5. symmetric permutation P A P^T with sorted rows
+    int32_t *prow, *plen, *pcol;
+    double *pval;
+    MPK_TRY(S.alloc(&prow, (size_t)n + 1));
+    MPK_TRY(S.alloc(&plen, (size_t)n + 1));
+    MPK_TRY(S.alloc(&pcol, (size_t)nnz));
+    MPK_TRY(S.alloc(&pval, (size_t)nnz));
+    MPK_CUDA(cudaMemsetAsync(plen + n, 0, sizeof(int32_t), st));
+    k_perm_len<<<blocks_for(n, 256), 256, 0, st>>>(n, A->rowptr, pl->d_perm, plen);
+    MPK_TRY(exclusive_scan<int32_t>(plen, prow, (int64_t)n + 1, st, nullptr));
+    k_perm_fill<<<blocks_for(n, 128), 128, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm, pl->d_iperm, prow,
+                                                    pcol, pval);
+
+    // 6. level sizes to the host
+    int64_t *d_lnnz;
+    MPK_TRY(S.alloc(&d_lnnz, (size_t)L));
+    k_level_nnz<<<blocks_for(L, 256), 256, 0, st>>>(L, pl->d_level_ptr, prow, d_lnnz);
+    std::vector<int64_t> lnnz((size_t)L);
+    pl->h_level_ptr.resize((size_t)L + 1);
+    MPK_CUDA(cudaMemcpyAsync(lnnz.data(), d_lnnz, sizeof(int64_t) * (size_t)L, cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaMemcpyAsync(pl->h_level_ptr.data(), pl->d_level_ptr, sizeof(int32_t) * ((size_t)L + 1),
+                             cudaMemcpyDeviceToHost, st));
+
+    // precision: bytes per stored entry (value + 32-bit column index)
+    int split_diag = 0;
+    if (pl->prec == MPK_F64) {
+        pl->val_bytes = 8;
+    } else if (pl->prec == MPK_F32) {
+        pl->val_bytes = 4;
+    } else {
+        int32_t *d_ne;
+        MPK_TRY(S.alloc(&d_ne, 1));
+        MPK_CUDA(cudaMemsetAsync(d_ne, 0, sizeof(int32_t), st));
+        k_bf16_exact<<<blocks_for(n, 256), 256, 0, st>>>(n, prow, pcol, pval, d_ne);
+        int32_t h_ne = 0;
+        MPK_CUDA(cudaMemcpyAsync(&h_ne, d_ne, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        split_diag = 1;
+        pl->val_bytes = h_ne ? 4 : 2;
+    }
+    pl->has_diag = split_diag;
+    MPK_CUDA(cudaStreamSynchronize(st));
+    for (int32_t l = 0; l < L; l++)
+        pl->max_level_rows = std::max(pl->max_level_rows, pl->h_level_ptr[l + 1] - pl->h_level_ptr[l]);
+
+    // 7. level groups (Eq. 5): add levels while (p+1) * weight(T) < f * C
+    {
+        const double budget = pl->safety_f * pl->cache_bytes;
+        const double bpe = (double)(pl->val_bytes + 4);
+        std::vector<int32_t> gp;
+        int32_t s0 = 0;
+        while (s0 < L) {
+            double acc = (double)lnnz[s0] * bpe;
+            int32_t e = s0 + 1;
+            while (e < L && (double)(p + 1) * (acc + (double)lnnz[e] * bpe) < budget) {
+                acc += (double)lnnz[e] * bpe;
+                e++;
+            }
+            gp.push_back(s0);
+            s0 = e;
+        }
+        gp.push_back(L);
+        pl->h_group_ptr = gp;
+        pl->n_groups = (int32_t)gp.size() - 1;
+    }
+
+    // 8. tiles (work items) inside groups, chunks of 32 rows inside tiles
+    int32_t tr = o->tile_rows;
+    if (tr <= 0) {
+        int64_t target = (int64_t)n / ((int64_t)pl->num_sms * 8);
+        tr = (int32_t)std::min<int64_t>(1024, std::max<int64_t>(kChunk, (target / kChunk) * kChunk));
+    }
+    tr = std::max(kChunk, (tr / kChunk) * kChunk);
+    pl->tile_rows = tr;
+    std::vector<int32_t> tile_row, tile_chunk, chunk_row, group_tile;
+    for (int32_t g = 0; g < pl->n_groups; g++) {
+        group_tile.push_back((int32_t)tile_row.size());
+        int32_t r0 = pl->h_level_ptr[pl->h_group_ptr[g]], r1 = pl->h_level_ptr[pl->h_group_ptr[g + 1]];
+        for (int32_t a = r0; a < r1; a += tr) {
+            int32_t b = std::min(r1, a + tr);
+            tile_row.push_back(a);
+            tile_chunk.push_back((int32_t)chunk_row.size());
+            for (int32_t c = a; c < b; c += kChunk) chunk_row.push_back(c);
+        }
+    }
+    group_tile.push_back((int32_t)tile_row.size());
+    tile_row.push_back(n);
+    tile_chunk.push_back((int32_t)chunk_row.size());
+    chunk_row.push_back(n);
+    pl->n_tiles = (int32_t)tile_row.size() - 1;
+    pl->n_chunks = (int32_t)chunk_row.size() - 1;
+    if ((int64_t)pl->n_tiles >= (1LL << 23)) return MPK_ERR_UNSUPPORTED;
+
+    int32_t *d_tile_row;
+    MPK_TRY(S.alloc(&d_tile_row, tile_row.size()));
+    MPK_TRY(dev_alloc(pl, &pl->d_tile_chunk, tile_chunk.size()));
+    MPK_TRY(dev_alloc(pl, &pl->d_chunk_row, chunk_row.size()));
+    MPK_TRY(dev_alloc(pl, &pl->d_chunk_off, chunk_row.size()));
+    MPK_TRY(dev_alloc(pl, &pl->d_group_ptr, pl->h_group_ptr.size()));
+    MPK_CUDA(cudaMemcpyAsync(d_tile_row, tile_row.data(), tile_row.size() * 4, cudaMemcpyHostToDevice, st));
+    MPK_CUDA(cudaMemcpyAsync(pl->d_tile_chunk, tile_chunk.data(), tile_chunk.size() * 4, cudaMemcpyHostToDevice, st));
+    MPK_CUDA(cudaMemcpyAsync(pl->d_chunk_row, chunk_row.data(), chunk_row.size() * 4, cudaMemcpyHostToDevice, st));
+    MPK_CUDA(cudaMemcpyAsync(pl->d_group_ptr, pl->h_group_ptr.data(), pl->h_group_ptr.size() * 4,
+                             cudaMemcpyHostToDevice, st));
+
+    // 9. packed SELL-32 matrix
+    int64_t *cw;
+    MPK_TRY(S.alloc(&cw, (size_t)pl->n_chunks + 1));
+    MPK_CUDA(cudaMemsetAsync(cw + pl->n_chunks, 0, sizeof(int64_t), st));
+    k_chunk_width<<<blocks_for(pl->n_chunks, 256), 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, prow, pcol,
+                                                                split_diag, cw);
+    int64_t total = 0;
+    MPK_TRY(exclusive_scan<int64_t>(cw, pl->d_chunk_off, (int64_t)pl->n_chunks + 1, st, &total));
+    pl->packed_entries = total;
+    MPK_TRY(dev_alloc(pl, &pl->d_pcol, (size_t)total));
+    if (split_diag) MPK_TRY(dev_alloc(pl, &pl->d_diag, (size_t)n));
+    {
+        const unsigned nbk = blocks_for((int64_t)pl->n_chunks * kChunk, 256);
+        if (pl->val_bytes == 8) {
+            double *v;
+            MPK_TRY(dev_alloc(pl, &v, (size_t)total));
+            pl->d_pval = v;
+            k_pack<double><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, prow, pcol, pval,
+                                                split_diag, pl->d_pcol, v, pl->d_diag);
+        } else if (pl->val_bytes == 4) {
+            float *v;
+            MPK_TRY(dev_alloc(pl, &v, (size_t)total));
+            pl->d_pval = v;
+            k_pack<float><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, prow, pcol, pval,
+                                               split_diag, pl->d_pcol, v, pl->d_diag);
+        } else {
+            __nv_bfloat16 *v;
+            MPK_TRY(dev_alloc(pl, &v, (size_t)total));
+            pl->d_pval = v;
+            k_pack<__nv_bfloat16><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, prow, pcol,
+                                                       pval, split_diag, pl->d_pcol, v, pl->d_diag);
+        }
+    }
+
+    // 10. dependency ranges of every tile
+    int32_t *tor;
+    MPK_TRY(S.alloc(&tor, (size_t)n));
+    MPK_TRY(dev_alloc(pl, &pl->d_dep_lo, (size_t)pl->n_tiles));
+    MPK_TRY(dev_alloc(pl, &pl->d_dep_hi, (size_t)pl->n_tiles));
+    k_tile_of_row<<<pl->n_tiles, 256, 0, st>>>(pl->n_tiles, d_tile_row, tor);
+    k_fill_i32<<<256, 256, 0, st>>>(pl->d_dep_lo, pl->n_tiles, INT_MAX);
+    k_fill_i32<<<256, 256, 0, st>>>(pl->d_dep_hi, pl->n_tiles, -1);
+    k_deps<<<blocks_for(n, 256), 256, 0, st>>>(n, prow, pcol, tor, A->assume_symmetric ? 1 : 0, pl->d_dep_lo,
+                                               pl->d_dep_hi);
+
+    // 11. work list in the diagonal order of the Lp diagram (Fig. 5) over level groups
+    {
+        const int32_t G = pl->n_groups;
+        std::vector<int32_t> work;
+        work.reserve((size_t)pl->n_tiles * p);
+        for (int32_t d = 1; d <= G + p - 1; d++) {
+            int32_t k0 = std::max(1, d - G + 1), k1 = std::min(d, p);
+            for (int32_t k = k0; k <= k1; k++) {
+                int32_t g = d - k;
+                for (int32_t t = group_tile[g]; t < group_tile[g + 1]; t++) work.push_back((t << 8) | k);
+            }
+        }
+        MPK_TRY(dev_alloc(pl, &pl->d_work, work.size()));
+        MPK_CUDA(cudaMemcpyAsync(pl->d_work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+    }
+    MPK_TRY(dev_alloc(pl, &pl->d_flags, (size_t)(p + 1) * pl->n_tiles));
+    MPK_TRY(dev_alloc(pl, &pl->d_ctl, CTL_WORDS));
+    MPK_CUDA(cudaMemsetAsync(pl->d_flags, 0, sizeof(uint32_t) * (size_t)(p + 1) * pl->n_tiles, st));
+    MPK_CUDA(cudaMemsetAsync(pl->d_ctl, 0, sizeof(int32_t) * CTL_WORDS, st));
+
+    int occ = 0;
+    MPK_TRY(wave_occupancy(pl, &occ));
+    int per_sm = o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : std::min(occ, 4);
+    pl->ctas_per_sm = std::max(1, per_sm);
+    int64_t items = (int64_t)pl->n_tiles * p;
+    pl->grid_ctas = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)pl->num_sms * pl->ctas_per_sm, items));
+
+    MPK_CUDA(cudaStreamSynchronize(st));
+    MPK_CUDA(cudaGetLastError());
+    pl->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    return MPK_OK;
+}
+
+}  // namespace
+
+int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st, int32_t *total) {
+    return exclusive_scan<int32_t>(in, out, n, st, total);
+}
+int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st, int64_t *total) {
+    return exclusive_scan<int64_t>(in, out, n, st, total);
+}
+
+}  // namespace mpk
+
+using namespace mpk;
+
+extern "C" {
+
+int mpk_opts_default(mpk_opts *o) {
+    if (!o) return MPK_ERR_INVALID;
+    memset(o, 0, sizeof(*o));
+    o->root = 0;
+    o->cache_bytes = 0.0;
+    o->safety_f = 0.5;
+    o->prec = MPK_F64;
+    o->nrhs = 1;
+    o->tile_rows = 0;
+    o->ctas_per_sm = 0;
+    o->timeout_s = 2.0;
+    o->stream = nullptr;
+    return MPK_OK;
+}
+
+int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out) {
+    if (!out) return MPK_ERR_INVALID;
+    *out = nullptr;
+    if (!A || !o || !A->rowptr || !A->col || !A->val) return MPK_ERR_INVALID;
+    if (A->n < 1 || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return MPK_ERR_INVALID;
+    if (p < 1 || p > kMaxP) return MPK_ERR_INVALID;
+    if (o->nrhs < 1 || o->nrhs > kMaxNrhs) return MPK_ERR_INVALID;
+    if (o->prec < MPK_F64 || o->prec > MPK_F32_BF16VAL) return MPK_ERR_INVALID;
+    if (!(o->safety_f > 0.0) || o->cache_bytes < 0.0 || o->tile_rows < 0 || o->ctas_per_sm < 0) return MPK_ERR_INVALID;
+    mpk_plan_s *h = new (std::nothrow) mpk_plan_s();
+    if (!h) return MPK_ERR_OOM;
+    int rc = build_plan(&h->pl, A, p, o);
+    if (rc != MPK_OK) {
+        cudaStreamSynchronize((cudaStream_t)o->stream);
+        free_plan(&h->pl);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return MPK_OK;
+}
+
+int mpk_plan_destroy(mpk_plan_t plan) {
+    if (!plan) return MPK_OK;
+    cudaStreamSynchronize(plan->pl.stream);
+    free_plan(&plan->pl);
+    delete plan;
+    return MPK_OK;
+}
+
+int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
+    if (!plan || !s) return MPK_ERR_INVALID;
+    const Plan &pl = plan->pl;
+    memset(s, 0, sizeof(*s));
+    s->n = pl.n;
+    s->p = pl.p;
+    s->nrhs = pl.nrhs;
+    s->prec = pl.prec;
+    s->nnz = pl.nnz;
+    s->n_levels = pl.n_levels;
+    s->n_groups = pl.n_groups;
+    s->n_tiles = pl.n_tiles;
+    s->max_level_rows = pl.max_level_rows;
+    s->tile_rows = pl.tile_rows;
+    s->grid_ctas = pl.grid_ctas;
+    s->val_bytes = pl.val_bytes;
+    s->packed_entries = pl.packed_entries;
+    s->matrix_bytes = pl.packed_entries * (int64_t)(pl.val_bytes + 4) + (pl.has_diag ? (int64_t)pl.n * 4 : 0);
+    s->device_bytes = pl.device_bytes + (int64_t)pl.io_bytes + (int64_t)pl.cheb_bytes;
+    s->plan_ms = pl.plan_ms;
+    s->cache_bytes = pl.cache_bytes;
+    return MPK_OK;
+}
+
+int mpk_plan_perm(mpk_plan_t plan, int32_t *perm, int32_t *level_ptr, int32_t *group_ptr, int32_t *level) {
+    if (!plan) return MPK_ERR_INVALID;
+    Plan &pl = plan->pl;
+    cudaStream_t st = pl.stream;
+    if (perm) MPK_CUDA(cudaMemcpyAsync(perm, pl.d_perm, sizeof(int32_t) * pl.n, cudaMemcpyDeviceToDevice, st));
+    if (level_ptr)
+        MPK_CUDA(cudaMemcpyAsync(level_ptr, pl.d_level_ptr, sizeof(int32_t) * (pl.n_levels + 1),
+                                 cudaMemcpyDeviceToDevice, st));
+    if (group_ptr)
+        MPK_CUDA(cudaMemcpyAsync(group_ptr, pl.d_group_ptr, sizeof(int32_t) * (pl.n_groups + 1),
+                                 cudaMemcpyDeviceToDevice, st));
+    if (level) MPK_CUDA(cudaMemcpyAsync(level, pl.d_level, sizeof(int32_t) * pl.n, cudaMemcpyDeviceToDevice, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    return MPK_OK;
+}
+
+const char *mpk_strerror(int status) {
+    switch (status) {
+    case MPK_OK: return "ok";
+    case MPK_ERR_INVALID: return "invalid argument or malformed matrix";
+    case MPK_ERR_CUDA: return "CUDA runtime error";
+    case MPK_ERR_OOM: return "out of memory";
+    case MPK_ERR_TIMEOUT: return "device-side dependency wait timed out";
+    case MPK_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

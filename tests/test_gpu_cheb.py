@@ -1,0 +1,59 @@
+"""GPU parity of the Chebyshev propagation (mpk_cheb, Sec. 7 Eq. 7-9) against
+the FP64 oracle, including sweeps with a remainder (M not a multiple of p)."""
+import numpy as np
+import pytest
+import torch
+
+import mpk_inputs as mi
+import oracle
+import paper_2205_01598_gb300 as mpk
+from gpu_helpers import plan_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(A, prec, p, M, permuted=False, rdt=50.0):
+    plan = plan_of(A, p, prec=prec, nrhs=2)
+    lo, hi = mpk.mpk_gershgorin(plan)
+    olo, ohi = oracle.gershgorin(A)
+    if prec == "f64":
+        assert (lo, hi) == (olo, ohi)
+    c, r = (ohi + olo) / 2, (ohi - olo) / 2
+    coef = oracle.cheb_coeffs_schroedinger(M, c, r, rdt / r)
+    psi = mi.uniform(1234, A.n) + 1j * mi.uniform(4321, A.n)
+    psi /= np.linalg.norm(psi)
+    ref = oracle.cheb(A, coef, c, r, psi)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    x = np.stack([psi.real, psi.imag], 1)
+    if permuted:
+        perm = mpk.mpk_plan_perm(plan)[0].cpu().numpy()
+        x = x[perm]
+        ref = ref[perm]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(dt).cuda()
+    yd = torch.empty(A.n, 2, dtype=torch.float64, device="cuda")
+    mpk.mpk_cheb(plan, coef, c, r, xd, yd, permuted=permuted)
+    y = yd.cpu().numpy()
+    got = y[:, 0] + 1j * y[:, 1]
+    return np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("p,M", [(8, 64), (5, 17), (1, 6), (16, 12)])
+def test_f64_cheb_matches_oracle(p, M):
+    A = mi.anderson3d(12, W=16.5, seed=42)
+    assert _run(A, "f64", p, M) <= 1e-12
+
+
+def test_f64_cheb_permuted_io():
+    A = mi.anderson3d(10, W=16.5, seed=42)
+    assert _run(A, "f64", 8, 64, permuted=True) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16val"])
+def test_reduced_precision_cheb_error_bound(prec):
+    """FP32 storage (BF16 hoppings for bf16val, exact for -1), FP64 scaling and
+    coefficient sum: relative error against the FP64 oracle <= 2e-5 for the
+    degree-64 Anderson propagation."""
+    A = mi.anderson3d(16, W=16.5, seed=42)
+    err = _run(A, prec, 8, 64)
+    print(prec, err)
+    assert err <= 2e-5
