@@ -56,6 +56,15 @@ typedef enum {
  *                  mpk_plan_stats.val_bytes).                                */
 typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
 
+/* Tuning bits of mpk_opts.tune (for autotuners; 0 = defaults).
+ *  MPK_TUNE_NO_STAGE    read the matrix slices straight from global memory
+ *                       instead of staging each work item's slice in shared
+ *                       memory with bulk (TMA) copies.
+ *  MPK_TUNE_EVICT_LAST  mark matrix slices evict-last in L2 until their last
+ *                       power (they are always marked evict-first then).    */
+#define MPK_TUNE_NO_STAGE   1u
+#define MPK_TUNE_EVICT_LAST 2u
+
 /* Flags of mpk_run / mpk_baseline_run / mpk_cheb. */
 #define MPK_IO_PERMUTED 1u  /* x and outputs are in the plan's level order   */
 #define MPK_ASYNC       2u  /* do not synchronise to read the device error word */
@@ -86,6 +95,10 @@ typedef struct {
     int32_t ctas_per_sm;   /* resident CTAs per SM of the wavefront; 0 = auto   */
     double timeout_s;      /* limit of every device-side wait; 0 = 2 seconds   */
     void *stream;          /* cudaStream_t for all work of this plan            */
+    double lag;            /* extra slope of the wavefront: how many level groups
+                              power k trails power k-1 beyond what the
+                              dependencies need; < 0 = automatic (default)     */
+    uint32_t tune;         /* MPK_TUNE_* bits                                   */
 } mpk_opts;
 
 /* Summary of a plan (all host values).                                    */
@@ -104,6 +117,9 @@ typedef struct {
     int64_t device_bytes;  /* all device memory held by the plan                 */
     double plan_ms;        /* wall time of mpk_plan                              */
     double cache_bytes;    /* C actually used in Eq. 5                           */
+    double slope;          /* sigma: level groups between consecutive power fronts */
+    int32_t staged;        /* 1 if work items stage their slice in shared memory */
+    int32_t smem_bytes;    /* dynamic shared memory per wavefront CTA            */
 } mpk_plan_stats;
 
 typedef struct mpk_plan_s *mpk_plan_t;

@@ -32,6 +32,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_CUDA, MPK_ERR_OOM, MPK_ERR_TIMEOUT, MPK_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 MPK_F64, MPK_F32, MPK_F32_BF16VAL = 0, 1, 2
 MPK_IO_PERMUTED, MPK_ASYNC = 1, 2
+MPK_TUNE_NO_STAGE, MPK_TUNE_EVICT_LAST = 1, 2
 PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL}
 
 
@@ -75,7 +76,8 @@ class mpk_csr(C.Structure):
 class mpk_opts(C.Structure):
     _fields_ = [("root", C.c_int32), ("cache_bytes", C.c_double), ("safety_f", C.c_double),
                 ("prec", C.c_int32), ("nrhs", C.c_int32), ("tile_rows", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+                ("ctas_per_sm", C.c_int32), ("timeout_s", C.c_double), ("stream", C.c_void_p),
+                ("lag", C.c_double), ("tune", C.c_uint32)]
 
 
 class mpk_plan_stats(C.Structure):
@@ -84,7 +86,8 @@ class mpk_plan_stats(C.Structure):
                 ("n_tiles", C.c_int32), ("max_level_rows", C.c_int32), ("tile_rows", C.c_int32),
                 ("grid_ctas", C.c_int32), ("val_bytes", C.c_int32), ("packed_entries", C.c_int64),
                 ("matrix_bytes", C.c_int64), ("device_bytes", C.c_int64), ("plan_ms", C.c_double),
-                ("cache_bytes", C.c_double)]
+                ("cache_bytes", C.c_double), ("slope", C.c_double), ("staged", C.c_int32),
+                ("smem_bytes", C.c_int32)]
 
 
 _lib = None
@@ -180,7 +183,8 @@ def mpk_opts_default():
 
 
 def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=0.0, safety_f=0.5,
-             prec="f64", nrhs=1, tile_rows=0, ctas_per_sm=0, timeout_s=2.0, stream=None) -> Plan:
+             prec="f64", nrhs=1, tile_rows=0, ctas_per_sm=0, timeout_s=2.0, lag=-1.0, tune=0,
+             stream=None) -> Plan:
     """Level-blocked plan of the CRS matrix (rowptr, col: int32 CUDA tensors,
     val: float64 CUDA tensor) for powers 1..p (mpk_plan)."""
     import torch
@@ -193,6 +197,8 @@ def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     o.nrhs, o.tile_rows, o.ctas_per_sm, o.timeout_s = int(nrhs), int(tile_rows), int(ctas_per_sm), float(timeout_s)
     o.stream = _stream(stream)
+    o.lag = float(lag)
+    o.tune = int(tune)
     h = C.c_void_p()
     _check(lib.mpk_plan(C.byref(A), int(p), C.byref(o), C.byref(h)), "mpk_plan")
     return Plan(h, int(p), int(nrhs), o.prec, A.n, stream)

@@ -9,25 +9,99 @@
 
 #include "mpk_internal.cuh"
 
+// Compile-time tuning of the wavefront kernels: entries of a row fetched per
+// batch for one vector column, and the minimum resident CTAs per SM that the
+// register allocation must allow (0 = no bound).
+#ifndef MPK_BATCH
+#define MPK_BATCH 8
+#endif
+#ifndef MPK_WAVE_MIN_BLOCKS
+#define MPK_WAVE_MIN_BLOCKS 0
+#endif
+
 namespace mpk {
 
 namespace {
 
 template <typename MT, typename VT>
 __device__ __forceinline__ VT to_vt(MT v) { return (VT)v; }
+template <>
+__device__ __forceinline__ float to_vt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <typename MT>
 __device__ __forceinline__ double as_double(MT v) { return (double)v; }
 template <>
 __device__ __forceinline__ double as_double<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
-template <>
-__device__ __forceinline__ float to_vt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---------------------------------------------------------------- TMA / mbarrier helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity` of an mbarrier.
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, uint64_t timeout_ns) {
+    if (mbar_try_wait(m, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(m, parity))
+        if (global_ns() - t0 > timeout_ns) return false;
+    return true;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_normal() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// Bulk (non-tensor) TMA copy global -> shared, completing on an mbarrier.
+// dst, src and bytes must be multiples of 16 bytes.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *m, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(m)), "l"(pol)
+        : "memory");
+}
+
+// Where a work item reads its slice of the packed matrix: global memory, or
+// the shared-memory stage that a bulk copy filled (entries base..).
+template <typename MT, bool STAGED>
+struct MatView {
+    const int32_t *col;
+    const MT *val;
+    int64_t base;
+    __device__ __forceinline__ int32_t c(int64_t i) const { return STAGED ? col[i - base] : __ldg(col + i); }
+    __device__ __forceinline__ MT v(int64_t i) const { return STAGED ? val[i - base] : __ldg(val + i); }
+};
 
 // y_out[r] = sum_j A[r, j] * y_in[j] for the (up to) 32 rows of SELL chunk c,
 // one row per lane (Fig. 1, restricted to the chunk's row range).  W columns
 // of the row-major block vectors are done per pass; EXACT means nrhs == W.
 // Padding entries (column -1) sit at the end of each row and are skipped.
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
-__device__ __forceinline__ void chunk_rows(const ExecArgs &a, int32_t c, int lane, const VT *yin, VT *yout) {
+template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED>
+__device__ __forceinline__ void chunk_rows(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t c, int lane,
+                                           const VT *yin, VT *yout) {
     const int32_t row0 = __ldg(a.chunk_row + c);
     const int32_t nrows = __ldg(a.chunk_row + c + 1) - row0;
     if (lane >= nrows) return;
@@ -35,21 +109,31 @@ __device__ __forceinline__ void chunk_rows(const ExecArgs &a, int32_t c, int lan
     const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
     const int32_t r = row0 + lane;
     const int nrhs = EXACT ? W : a.nrhs;
-    const int32_t *cp = a.pcol + off + lane;
-    const MT *vp = (const MT *)a.pval + off + lane;
+    const int64_t e0 = off + lane;
+    // B entries of the row are fetched together (indices and values first,
+    // then the B gathers) so that each lane keeps many loads in flight.
+    constexpr int B = W <= 2 ? MPK_BATCH : (W <= 4 ? 4 : 2);
     for (int cb = 0; cb < nrhs; cb += W) {
         VT acc[W];
 #pragma unroll
         for (int i = 0; i < W; i++) acc[i] = VT(0);
-#pragma unroll 4
-        for (int32_t j = 0; j < w; j++) {
-            const int32_t col = __ldg(cp + (int64_t)j * kChunk);
-            const VT v = to_vt<MT, VT>(__ldg(vp + (int64_t)j * kChunk));
-            if (col >= 0) {
-                const VT *src = yin + (int64_t)col * nrhs + cb;
+        for (int32_t j0 = 0; j0 < w; j0 += B) {
+            int32_t cols[B];
+            VT vals[B];
 #pragma unroll
-                for (int i = 0; i < W; i++)
-                    if (EXACT || cb + i < nrhs) acc[i] = fma(v, src[i], acc[i]);
+            for (int u = 0; u < B; u++) {
+                const bool in = j0 + u < w;
+                cols[u] = in ? mv.c(e0 + (int64_t)(j0 + u) * kChunk) : -1;
+                vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(j0 + u) * kChunk)) : VT(0);
+            }
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                if (cols[u] >= 0) {
+                    const VT *src = yin + (int64_t)cols[u] * nrhs + cb;
+#pragma unroll
+                    for (int i = 0; i < W; i++)
+                        if (EXACT || cb + i < nrhs) acc[i] = fma(vals[u], src[i], acc[i]);
+                }
             }
         }
         if (DIAG) {
@@ -66,53 +150,176 @@ __device__ __forceinline__ void chunk_rows(const ExecArgs &a, int32_t c, int lan
     }
 }
 
-// Warp 0 of a CTA waits until power k-1 is complete on every tile in
-// [dep_lo[t], dep_hi[t]] (the tiles holding the columns of tile t: the
-// conditions (A)-(C) of Sec. 4.3 at tile granularity).  Bounded: after
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t *p) {
+    uint4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+// Dependency check of a work item (tile t, power k), run by warp 0: power
+// k-1 must be complete on every tile in [dep_lo[t], dep_hi[t]] (the tiles
+// holding the columns of tile t; conditions (A)-(C) of Sec. 4.3 at tile
+// granularity).  The flags of the next item are loaded (16-byte relaxed loads,
+// 4 flags each) before the current item is computed, so that in steady state
+// the check costs no round trip.  Flag rows are padded so that a 16-byte load
+// that starts at a multiple of 4 inside [lo, hi] stays in bounds.
+constexpr int kProbeVec = 2;   // 2 x 32 lanes x 4 flags = 256 flags per probe
+
+struct FlagProbe {
+    uint4 v[kProbeVec];
+    int32_t lo, hi, base;
+
+    __device__ __forceinline__ void issue(const ExecArgs &a, int32_t t, int32_t k, int lane) {
+        lo = __ldg(a.dep_lo + t);
+        hi = __ldg(a.dep_hi + t);
+        base = lo & ~3;
+        const uint32_t *f = a.flags + (int64_t)(k - 1) * a.fstride;
+#pragma unroll
+        for (int q = 0; q < kProbeVec; q++) {
+            const int32_t i = base + (q * 32 + lane) * 4;
+            v[q] = i <= hi ? ld_relaxed_v4(f + i) : make_uint4(0, 0, 0, 0);
+        }
+    }
+    __device__ __forceinline__ bool fits() const { return hi - base < kProbeVec * 128; }
+    __device__ __forceinline__ bool ready(uint32_t epoch, int lane) const {
+        bool good = true;
+#pragma unroll
+        for (int q = 0; q < kProbeVec; q++) {
+            const int32_t i = base + (q * 32 + lane) * 4;
+            const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+            for (int s = 0; s < 4; s++)
+                if (i + s >= lo && i + s <= hi) good &= (w[s] == epoch);
+        }
+        return __all_sync(0xffffffffu, good);
+    }
+};
+
+// Bounded check for a range wider than one probe (huge levels, small tiles).
+__device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch, int lane) {
+    const uint32_t *f = a.flags + (int64_t)(k - 1) * a.fstride;
+    const int32_t lo = __ldg(a.dep_lo + t), hi = __ldg(a.dep_hi + t);
+    bool ok = true;
+    for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (ld_relaxed_u32(f + i) == epoch);
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ void record_timeout(const ExecArgs &a, int32_t k, int32_t t) {
+    if (atomicCAS(a.ctl + CTL_ERR, 0, (int)MPK_ERR_TIMEOUT) == 0) {
+        atomicExch(a.ctl + CTL_ERR_K, k);
+        atomicExch(a.ctl + CTL_ERR_T, t);
+    }
+    atomicExch(a.ctl + CTL_ABORT, 1);
+}
+
+// Polls until the item's dependencies are complete.  Bounded: after
 // timeout_ns it records MPK_ERR_TIMEOUT with the node, raises the abort word
 // and returns false; it also returns false once another CTA has aborted.
-__device__ bool wait_deps(const ExecArgs &a, int32_t k, int32_t t, uint32_t epoch, int lane) {
-    const uint32_t *f = a.flags + (int64_t)(k - 1) * a.n_tiles;
-    const int32_t lo = __ldg(a.dep_lo + t), hi = __ldg(a.dep_hi + t);
-    uint64_t t0 = 0;
+__device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k, uint32_t epoch, int lane) {
+    const bool wide = !pr.fits();
+    if (wide ? ready_wide(a, t, k, epoch, lane) : pr.ready(epoch, lane)) {
+        fence_acq_rel_gpu();
+        return true;
+    }
+    const uint64_t t0 = global_ns();
     unsigned ns = 32;
-    for (int it = 0;; it++) {
-        bool ok = true;
-        for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (ld_relaxed_u32(f + i) == epoch);
-        if (__all_sync(0xffffffffu, ok)) break;
+    for (;;) {
         int stop = 0;
         if (lane == 0) {
-            if (it == 0) t0 = global_ns();
             if (ld_relaxed_s32(a.ctl + CTL_ABORT)) {
                 stop = 1;
-            } else if (it > 0 && global_ns() - t0 > a.timeout_ns) {
-                if (atomicCAS(a.ctl + CTL_ERR, 0, (int)MPK_ERR_TIMEOUT) == 0) {
-                    atomicExch(a.ctl + CTL_ERR_K, k);
-                    atomicExch(a.ctl + CTL_ERR_T, t);
-                }
-                atomicExch(a.ctl + CTL_ABORT, 1);
+            } else if (global_ns() - t0 > a.timeout_ns) {
+                record_timeout(a, k, t);
                 stop = 1;
             }
         }
         if (__shfl_sync(0xffffffffu, stop, 0)) return false;
         __nanosleep(ns);
-        if (ns < 512) ns <<= 1;
+        if (ns < 256) ns <<= 1;
+        if (wide) {
+            if (ready_wide(a, t, k, epoch, lane)) break;
+        } else {
+            pr.issue(a, t, k, lane);
+            if (pr.ready(epoch, lane)) break;
+        }
     }
     fence_acq_rel_gpu();
     return true;
 }
 
-// The last CTA to leave resets the dispatch words and publishes the epoch.
-__device__ __forceinline__ void wave_teardown(const ExecArgs &a, uint32_t epoch) {
-    if (threadIdx.x == 0) {
-        __threadfence();
-        int done = atomicAdd(a.ctl + CTL_FINISHED, 1);
-        if (done == (int)gridDim.x - 1) {
-            atomicExch(a.ctl + CTL_NEXT, 0);
-            atomicExch(a.ctl + CTL_FINISHED, 0);
-            atomicExch(a.ctl + CTL_ABORT, 0);
-            atomicExch(a.ctl + CTL_EPOCH, (int)epoch);
-            __threadfence();
+// Bulk copy of the packed slice of work item wk (columns, then values) into
+// a shared-memory stage.  The L2 hint marks the slice evict-first at its last
+// power (no later reuse) and evict-last before (it is read again p-1 times).
+template <typename MT>
+__device__ __forceinline__ void stage_item(const ExecArgs &a, int32_t wk, unsigned char *stage, uint64_t *mbar) {
+    const int32_t t = wk >> 8, k = wk & 255;
+    const int64_t o0 = __ldg(a.tile_off + t), o1 = __ldg(a.tile_off + t + 1);
+    const uint32_t ne = (uint32_t)(o1 - o0);
+    const uint64_t pol = k >= a.p ? l2_policy_evict_first()
+                                  : ((a.tune & MPK_TUNE_EVICT_LAST) ? l2_policy_evict_last() : l2_policy_evict_normal());
+    fence_proxy_async_smem();
+    mbar_expect_tx(mbar, ne * (uint32_t)(4 + sizeof(MT)));
+    bulk_g2s(stage, a.pcol + o0, ne * 4u, mbar, pol);
+    bulk_g2s(stage + (size_t)a.stage_entries * 4, (const MT *)a.pval + o0, ne * (uint32_t)sizeof(MT), mbar, pol);
+}
+
+// Single-vector rows of up to kCpw chunks of one warp with the matrix slice
+// in shared memory: the gathers of all chunks (kGb entries of each row per
+// pass) are issued before any of them is used, so that an item costs about
+// one gather round trip instead of one per chunk.
+constexpr int kCpw = 2;   // chunks of a warp handled together
+constexpr int kGb = 8;    // entries per row per pass
+
+template <typename VT, typename MT, bool DIAG>
+__device__ __forceinline__ void warp_chunks_staged(const ExecArgs &a, const MatView<MT, true> &mv, int32_t c0,
+                                                   int32_t c1, int ncw, int lane, const VT *yin, VT *yout) {
+    for (int32_t cb = c0; cb < c1; cb += kCpw * ncw) {
+        int32_t row[kCpw], w[kCpw];
+        int64_t e0[kCpw];
+        int32_t wmax = 0;
+#pragma unroll
+        for (int i = 0; i < kCpw; i++) {
+            const int32_t c = cb + i * ncw;
+            row[i] = -1;
+            w[i] = 0;
+            e0[i] = 0;
+            if (c < c1) {
+                const int32_t r0 = __ldg(a.chunk_row + c);
+                const int64_t off = __ldg(a.chunk_off + c);
+                if (lane < __ldg(a.chunk_row + c + 1) - r0) {
+                    row[i] = r0 + lane;
+                    w[i] = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
+                    e0[i] = off + lane;
+                }
+            }
+            wmax = max(wmax, w[i]);
+        }
+        VT acc[kCpw];
+#pragma unroll
+        for (int i = 0; i < kCpw; i++) acc[i] = VT(0);
+        for (int32_t j0 = 0; j0 < wmax; j0 += kGb) {
+            VT g[kCpw][kGb];
+#pragma unroll
+            for (int i = 0; i < kCpw; i++)
+#pragma unroll
+                for (int u = 0; u < kGb; u++) {
+                    const int32_t col = j0 + u < w[i] ? mv.c(e0[i] + (int64_t)(j0 + u) * kChunk) : -1;
+                    g[i][u] = col >= 0 ? yin[col] : VT(0);
+                }
+#pragma unroll
+            for (int i = 0; i < kCpw; i++)
+#pragma unroll
+                for (int u = 0; u < kGb; u++)
+                    if (j0 + u < w[i]) acc[i] = fma(to_vt<MT, VT>(mv.v(e0[i] + (int64_t)(j0 + u) * kChunk)), g[i][u], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kCpw; i++) {
+            if (row[i] < 0) continue;
+            if (DIAG) acc[i] = fma((VT)__ldg(a.diag + row[i]), yin[row[i]], acc[i]);
+            yout[row[i]] = acc[i];
         }
     }
 }
@@ -120,87 +327,210 @@ __device__ __forceinline__ void wave_teardown(const ExecArgs &a, uint32_t epoch)
 // Body of one work item (tile t, power k) of the plain MPK.
 template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
 struct MpkNode {
-    __device__ __forceinline__ static void run(const ExecArgs &a, int32_t t, int32_t k, int warp, int nwarps, int lane) {
+    template <bool STAGED>
+    __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t k,
+                                               int warp, int nwarps, int lane, const int &) {
         const VT *yin = k == 1 ? (const VT *)a.x : (const VT *)a.Y + (int64_t)(k - 2) * a.blk;
         VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
         const int32_t c1 = __ldg(a.tile_chunk + t + 1);
-        for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps)
-            chunk_rows<VT, MT, W, EXACT, DIAG>(a, c, lane, yin, yout);
+        if constexpr (STAGED && W == 1 && EXACT) {
+            warp_chunks_staged<VT, MT, DIAG>(a, mv, __ldg(a.tile_chunk + t) + warp, c1, nwarps, lane, yin, yout);
+        } else {
+            for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps)
+                chunk_rows<VT, MT, W, EXACT, DIAG, STAGED>(a, mv, c, lane, yin, yout);
+        }
     }
 };
 
-// Persistent wavefront: CTAs take work items in the order of the Lp diagram
-// over level groups (diagonals ascending, powers ascending inside a
-// diagonal, tiles ascending inside a group).  Items are handed out in order
-// by one counter, so every item's dependencies were taken earlier by running
-// CTAs and the launch cannot deadlock even when not all CTAs are resident.
-template <typename Node, typename Extra>
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+constexpr int kBarReady = 1;   // scheduler -> compute warps: the next item may start
+constexpr int kBarDone = 2;    // compute warps -> scheduler: the current item is finished
+
+// Persistent, warp-specialised wavefront.  Work items are dealt round-robin
+// in the issue order (item j goes to CTA j mod gridDim.x; each CTA runs its
+// items in order).  Every dependency of an item comes earlier in that order,
+// the launch is cooperative (all CTAs resident), and a CTA publishes a
+// finished item before it blocks on the dependencies of its next one, so the
+// lowest unfinished item can always run: the launch cannot deadlock.
+//
+// The last warp of the CTA schedules: it checks the dependencies of the next
+// item (flags loaded ahead of time), performs the acquire fence, has the
+// item's matrix slice copied into a shared-memory stage (bulk copy, staged
+// form), starts the compute warps, and publishes the previous item with a
+// release store.  Its fences overlap the compute warps' work instead of
+// stalling them.
+template <typename Node, typename MT, bool STAGED, typename Extra>
 __device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra) {
-    __shared__ int s_item[2];
-    __shared__ int s_ok;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    __shared__ int s_item, s_stage;
+    __shared__ __align__(8) uint64_t mbar[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncw = (int)(blockDim.x >> 5) - 1;
+    const int nthr = (int)blockDim.x;
     const uint32_t epoch = (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u;
-    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl + CTL_NEXT, 1);
+    const size_t stage_bytes = STAGED ? (size_t)a.stage_entries * (4 + sizeof(MT)) : 0;
+    if (STAGED && threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
-    int cur = s_item[0], buf = 1;
-    while (cur < a.n_items) {
-        if (threadIdx.x == 0) s_item[buf] = ld_relaxed_s32(a.ctl + CTL_ABORT) ? INT_MAX : atomicAdd(a.ctl + CTL_NEXT, 1);
-        const int32_t wk = __ldg(a.work + cur);
-        const int32_t t = wk >> 8, k = wk & 255;
-        if (k <= a.p) {
-            if (warp == 0) {
-                bool ok = k == 1 ? true : wait_deps(a, k, t, epoch, lane);
-                if (lane == 0) s_ok = ok;
+
+    if (warp == ncw) {
+        // ------------------------------------------------------------ scheduler warp
+        const int G = (int)gridDim.x;
+        int32_t issued[2] = {0, 0}, consumed[2] = {0, 0};   // bulk copies per stage
+        auto issue = [&](int32_t jj, int st) {
+            if (STAGED) {
+                if (lane == 0) stage_item<MT>(a, __ldg(a.work + jj), dsmem + st * stage_bytes, &mbar[st]);
+                issued[st]++;
             }
-            __syncthreads();
-            if (s_ok) {
-                Node::run(a, t, k, warp, nwarps, lane, extra);
-                __syncthreads();
-                if (threadIdx.x == 0 && !(t == a.drop_tile && k == a.drop_k)) {
-                    fence_acq_rel_gpu();
-                    st_release_u32(a.flags + (int64_t)k * a.n_tiles + t, epoch);
-                }
+        };
+        FlagProbe pr;
+        int32_t j = blockIdx.x;
+        bool ok = j < a.n_items;
+        if (ok) {
+            issue(j, 0);
+            if (j + G < a.n_items) issue(j + G, 1);
+            const int32_t wk = __ldg(a.work + j);
+            if ((wk & 255) > 1) {
+                pr.issue(a, wk >> 8, wk & 255, lane);
+                ok = wait_deps(a, pr, wk >> 8, wk & 255, epoch, lane);
             }
         }
-        __syncthreads();
-        cur = s_item[buf];
-        buf ^= 1;
+        if (lane == 0) {
+            s_item = ok ? __ldg(a.work + j) : -1;
+            s_stage = 0;
+        }
+        __syncwarp();
+        named_arrive(kBarReady, nthr);
+        int32_t i = 0;
+        while (ok) {
+            const int32_t wk = __ldg(a.work + j);
+            const int32_t jn = j + G;
+            int32_t wn = 0;
+            bool ready = true;
+            if (jn < a.n_items) {
+                wn = __ldg(a.work + jn);
+                if ((wn & 255) > 1) {
+                    pr.issue(a, wn >> 8, wn & 255, lane);
+                    ready = pr.fits() ? pr.ready(epoch, lane) : ready_wide(a, wn >> 8, wn & 255, epoch, lane);
+                    if (ready) fence_acq_rel_gpu();
+                }
+            }
+            named_sync(kBarDone, nthr);   // compute warps finished item j
+            if (STAGED) consumed[i & 1]++;
+            auto publish = [&]() {
+                const int32_t t = wk >> 8, k = wk & 255;
+                if (lane == 0 && !(t == a.drop_tile && k == a.drop_k))
+                    st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
+            };
+            if (jn >= a.n_items) {
+                publish();
+                if (lane == 0) s_item = -1;
+                __syncwarp();
+                named_arrive(kBarReady, nthr);
+                break;
+            }
+            if (!ready) {   // publish first, then block on the next item's dependencies
+                publish();
+                ready = wait_deps(a, pr, wn >> 8, wn & 255, epoch, lane);
+            }
+            if (ready && j + 2 * G < a.n_items) issue(j + 2 * G, i & 1);   // stage of item j is free
+            if (lane == 0) {
+                s_item = ready ? wn : -1;
+                s_stage = (i + 1) & 1;
+            }
+            __syncwarp();
+            named_arrive(kBarReady, nthr);
+            if (!ready) break;
+            publish();   // off the compute warps' critical path (a repeat store is harmless)
+            j = jn;
+            i++;
+        }
+        // never leave with a bulk copy in flight (abort path)
+        for (int st = 0; STAGED && st < 2; st++)
+            while (consumed[st] < issued[st]) {
+                if (!mbar_wait(&mbar[st], (uint32_t)(consumed[st] & 1), a.timeout_ns) && lane == 0)
+                    record_timeout(a, 0, -1);
+                consumed[st]++;
+            }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            const int done = atomicAdd(a.ctl + CTL_FINISHED, 1);
+            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch, reset
+                atomicExch(a.ctl + CTL_FINISHED, 0);
+                atomicExch(a.ctl + CTL_ABORT, 0);
+                atomicExch(a.ctl + CTL_EPOCH, (int)epoch);
+                __threadfence();
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ compute warps
+        uint32_t ph0 = 0, ph1 = 0;
+        for (;;) {
+            named_sync(kBarReady, nthr);
+            const int32_t wk = *(volatile int *)&s_item;
+            const int st = *(volatile int *)&s_stage;
+            if (wk < 0) break;
+            const int32_t t = wk >> 8, k = wk & 255;
+            if (STAGED) {
+                const bool landed = mbar_wait(&mbar[st], st ? ph1 : ph0, a.timeout_ns);
+                if (st) ph1 ^= 1u; else ph0 ^= 1u;
+                if (!landed) {
+                    if (lane == 0) record_timeout(a, k, t);
+                    named_arrive(kBarDone, nthr);
+                    continue;
+                }
+            }
+            const MatView<MT, STAGED> mv{STAGED ? (const int32_t *)(dsmem + st * stage_bytes) : a.pcol,
+                                         STAGED ? (const MT *)(dsmem + st * stage_bytes + (size_t)a.stage_entries * 4)
+                                                : (const MT *)a.pval,
+                                         STAGED ? __ldg(a.tile_off + t) : 0};
+            Node::template run<STAGED>(a, mv, t, k, warp, ncw, lane, extra);
+            named_arrive(kBarDone, nthr);
+        }
     }
-    wave_teardown(a, epoch);
 }
 
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
-struct MpkNodeX {
-    __device__ __forceinline__ static void run(const ExecArgs &a, int32_t t, int32_t k, int warp, int nwarps, int lane,
-                                               const int &) {
-        MpkNode<VT, MT, W, EXACT, DIAG>::run(a, t, k, warp, nwarps, lane);
-    }
-};
-
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
-__global__ void __launch_bounds__(kWaveThreads) k_wave(ExecArgs a) {
-    wave_loop<MpkNodeX<VT, MT, W, EXACT, DIAG>, int>(a, 0);
+#if MPK_WAVE_MIN_BLOCKS > 0
+#define MPK_WAVE_BOUNDS __launch_bounds__(kWaveThreads, MPK_WAVE_MIN_BLOCKS)
+#else
+#define MPK_WAVE_BOUNDS __launch_bounds__(kWaveThreads)
+#endif
+template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED>
+__global__ void MPK_WAVE_BOUNDS k_wave(ExecArgs a) {
+    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED, int>(a, 0);
 }
 
 // Baseline: one SpMV over all chunks (warp per chunk, grid-stride).
 template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
-__global__ void __launch_bounds__(kWaveThreads) k_spmv(ExecArgs a, const VT *yin, VT *yout) {
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(ExecArgs a, const VT *yin, VT *yout) {
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = gw; c < a.n_chunks; c += nw) chunk_rows<VT, MT, W, EXACT, DIAG>(a, (int32_t)c, lane, yin, yout);
+    const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
+    for (int64_t c = gw; c < a.n_chunks; c += nw)
+        chunk_rows<VT, MT, W, EXACT, DIAG, false>(a, mv, (int32_t)c, lane, yin, yout);
 }
 
 // ---------------------------------------------------------------- Chebyshev
-// Node of sweep powers: global power k = k0 + j.  With Ahat = (A - c)/r:
+// Node of a sweep: global power k = k0 + j.  With Ahat = (A - c)/r:
 //   v_1 = Ahat v_0,  v_k = 2 Ahat v_{k-1} - v_{k-2},  acc += coef_k v_k,
 // vectors complex (two columns re, im) in a ring of three blocks; A v is
 // summed in the storage precision, the scaling, the recurrence update and
 // the coefficient sum are done in FP64.
 template <typename VT, typename MT, bool DIAG>
 struct ChebNode {
-    __device__ __forceinline__ static void run(const ExecArgs &a, int32_t t, int32_t j, int warp, int nwarps, int lane,
-                                               const ChebArgs &ca) {
+    template <bool STAGED>
+    __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t j,
+                                               int warp, int nwarps, int lane, const ChebArgs &ca) {
         const int32_t k = ca.k0 + j;
         VT *ring = (VT *)ca.ring;
         const VT *yin = ring + (int64_t)((k - 1) % 3) * a.blk;
@@ -215,16 +545,24 @@ struct ChebNode {
             const int64_t off = __ldg(a.chunk_off + c);
             const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
             const int32_t r = row0 + lane;
-            const int32_t *cp = a.pcol + off + lane;
-            const MT *vp = (const MT *)a.pval + off + lane;
+            const int64_t e0 = off + lane;
             VT s0 = VT(0), s1 = VT(0);
-#pragma unroll 4
-            for (int32_t q = 0; q < w; q++) {
-                const int32_t col = __ldg(cp + (int64_t)q * kChunk);
-                const VT v = to_vt<MT, VT>(__ldg(vp + (int64_t)q * kChunk));
-                if (col >= 0) {
-                    s0 = fma(v, yin[2 * (int64_t)col], s0);
-                    s1 = fma(v, yin[2 * (int64_t)col + 1], s1);
+            constexpr int B = 8;
+            for (int32_t q0 = 0; q0 < w; q0 += B) {
+                int32_t cols[B];
+                VT vals[B];
+#pragma unroll
+                for (int u = 0; u < B; u++) {
+                    const bool in = q0 + u < w;
+                    cols[u] = in ? mv.c(e0 + (int64_t)(q0 + u) * kChunk) : -1;
+                    vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(q0 + u) * kChunk)) : VT(0);
+                }
+#pragma unroll
+                for (int u = 0; u < B; u++) {
+                    if (cols[u] >= 0) {
+                        s0 = fma(vals[u], yin[2 * (int64_t)cols[u]], s0);
+                        s1 = fma(vals[u], yin[2 * (int64_t)cols[u] + 1], s1);
+                    }
                 }
             }
             const double u0 = (double)yin[2 * (int64_t)r], u1 = (double)yin[2 * (int64_t)r + 1];
@@ -251,9 +589,9 @@ struct ChebNode {
     }
 };
 
-template <typename VT, typename MT, bool DIAG>
+template <typename VT, typename MT, bool DIAG, bool STAGED>
 __global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
-    wave_loop<ChebNode<VT, MT, DIAG>, ChebArgs>(ca.e, ca);
+    wave_loop<ChebNode<VT, MT, DIAG>, MT, STAGED, ChebArgs>(ca.e, ca);
 }
 
 // acc = coef_0 * v_0 (complex), v_0 = ring block 0
@@ -318,14 +656,14 @@ __global__ void k_permute(int32_t n, int32_t words, int32_t count, const int32_t
 }
 
 // ---------------------------------------------------------------- dispatch
-template <typename VT, typename MT, bool DIAG>
+template <typename VT, typename MT, bool DIAG, bool STAGED>
 const void *wave_ptr(int nrhs) {
     switch (nrhs) {
-    case 1: return (const void *)k_wave<VT, MT, 1, true, DIAG>;
-    case 2: return (const void *)k_wave<VT, MT, 2, true, DIAG>;
-    case 4: return (const void *)k_wave<VT, MT, 4, true, DIAG>;
-    case 8: return (const void *)k_wave<VT, MT, 8, true, DIAG>;
-    default: return (const void *)k_wave<VT, MT, 8, false, DIAG>;
+    case 1: return (const void *)k_wave<VT, MT, 1, true, DIAG, STAGED>;
+    case 2: return (const void *)k_wave<VT, MT, 2, true, DIAG, STAGED>;
+    case 4: return (const void *)k_wave<VT, MT, 4, true, DIAG, STAGED>;
+    case 8: return (const void *)k_wave<VT, MT, 8, true, DIAG, STAGED>;
+    default: return (const void *)k_wave<VT, MT, 8, false, DIAG, STAGED>;
     }
 }
 template <typename VT, typename MT, bool DIAG>
@@ -339,36 +677,45 @@ const void *spmv_ptr(int nrhs) {
     }
 }
 
-const void *pick_wave(const Plan *pl) {
-    if (pl->prec == MPK_F64) return wave_ptr<double, double, false>(pl->nrhs);
-    if (!pl->has_diag) return wave_ptr<float, float, false>(pl->nrhs);
-    if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true>(pl->nrhs);
-    return wave_ptr<float, float, true>(pl->nrhs);
+template <bool STAGED>
+const void *pick_wave_t(const Plan *pl) {
+    if (pl->prec == MPK_F64) return wave_ptr<double, double, false, STAGED>(pl->nrhs);
+    if (!pl->has_diag) return wave_ptr<float, float, false, STAGED>(pl->nrhs);
+    if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, STAGED>(pl->nrhs);
+    return wave_ptr<float, float, true, STAGED>(pl->nrhs);
 }
+template <bool STAGED>
+const void *pick_cheb_t(const Plan *pl) {
+    if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false, STAGED>;
+    if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED>;
+    if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED>;
+    return (const void *)k_cheb_wave<float, float, true, STAGED>;
+}
+const void *pick_wave(const Plan *pl) { return pl->staged ? pick_wave_t<true>(pl) : pick_wave_t<false>(pl); }
+const void *pick_cheb(const Plan *pl) { return pl->staged ? pick_cheb_t<true>(pl) : pick_cheb_t<false>(pl); }
 const void *pick_spmv(const Plan *pl) {
     if (pl->prec == MPK_F64) return spmv_ptr<double, double, false>(pl->nrhs);
     if (!pl->has_diag) return spmv_ptr<float, float, false>(pl->nrhs);
     if (pl->val_bytes == 2) return spmv_ptr<float, __nv_bfloat16, true>(pl->nrhs);
     return spmv_ptr<float, float, true>(pl->nrhs);
 }
-const void *pick_cheb(const Plan *pl) {
-    if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false>;
-    if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false>;
-    if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true>;
-    return (const void *)k_cheb_wave<float, float, true>;
-}
 
 }  // namespace
 
+// Resident CTAs per SM of the wavefront kernels of this plan (with the
+// dynamic shared memory of the staged form); also raises the kernels' limit
+// of dynamic shared memory to what the plan needs.
 int wave_occupancy(const Plan *pl, int *ctas_per_sm) {
-    int occ = 0;
-    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_wave(pl), kWaveThreads, 0));
-    int occ2 = 0;
-    if (pl->nrhs == 2) {
-        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, pick_cheb(pl), kWaveThreads, 0));
-        occ = std::min(occ, occ2);
+    const void *fns[2] = {pick_wave(pl), pl->nrhs == 2 ? pick_cheb(pl) : nullptr};
+    int occ = 1 << 30;
+    for (const void *fn : fns) {
+        if (!fn) continue;
+        MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes));
+        int o = 0;
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kWaveThreads, pl->smem_bytes));
+        occ = std::min(occ, o);
     }
-    *ctas_per_sm = std::max(1, occ);
+    *ctas_per_sm = occ;
     return MPK_OK;
 }
 
@@ -384,6 +731,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.pval = pl->d_pval;
     a.diag = pl->d_diag;
     a.flags = pl->d_flags;
+    a.fstride = pl->fstride;
     a.ctl = pl->d_ctl;
     a.n_tiles = pl->n_tiles;
     a.n_items = pl->n_tiles * pl->p;
@@ -396,13 +744,33 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.timeout_ns = (uint64_t)(pl->timeout_s * 1e9);
     a.drop_tile = -1;
     a.drop_k = -1;
+    a.tile_off = pl->d_tile_off;
+    a.stage_entries = pl->stage_entries;
+    a.tune = pl->tune;
     return a;
+}
+
+// Cooperative launch (all CTAs co-resident), expressed with cudaLaunchKernelEx
+// so that it can also be captured in a CUDA graph.
+static int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kWaveThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    MPK_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+    return MPK_OK;
 }
 
 // Epochs are 32-bit: before they could wrap onto stale flag values, clear all.
 static int epoch_guard(Plan *pl, cudaStream_t st) {
     if (pl->launches >= 0xFFFFFF00ull) {
-        MPK_CUDA(cudaMemsetAsync(pl->d_flags, 0, sizeof(uint32_t) * (size_t)(pl->p + 1) * pl->n_tiles, st));
+        MPK_CUDA(cudaMemsetAsync(pl->d_flags, 0, sizeof(uint32_t) * (size_t)(pl->p + 1) * pl->fstride, st));
         MPK_CUDA(cudaMemsetAsync(pl->d_ctl, 0, sizeof(int32_t) * CTL_WORDS, st));
         pl->launches = 0;
     }
@@ -418,24 +786,24 @@ int launch_wavefront(Plan *pl, const void *x, void *Y, cudaStream_t st) {
     a.drop_k = pl->drop_k;
     pl->drop_tile = pl->drop_k = -1;
     void *args[] = {(void *)&a};
-    MPK_CUDA(cudaLaunchKernel(pick_wave(pl), dim3(pl->grid_ctas), dim3(kWaveThreads), args, 0, st));
-    return MPK_OK;
+    return launch_coop(pick_wave(pl), pl->grid_ctas, pl->smem_bytes, args, st);
 }
 
 int launch_baseline(Plan *pl, const void *x, void *Y, cudaStream_t st) {
     ExecArgs a = exec_args(pl, x, Y);
     const void *fn = pick_spmv(pl);
     int occ = 0;
-    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kWaveThreads, 0));
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSpmvThreads, 0));
     int64_t warps_needed = pl->n_chunks;
-    int64_t grid = std::min<int64_t>((int64_t)pl->num_sms * std::max(1, occ), (warps_needed + 7) / 8);
+    const int wpb = kSpmvThreads / 32;
+    int64_t grid = std::min<int64_t>((int64_t)pl->num_sms * std::max(1, occ), (warps_needed + wpb - 1) / wpb);
     grid = std::max<int64_t>(1, grid);
     const size_t eb = (size_t)elem_bytes_of(pl);
     for (int k = 1; k <= pl->p; k++) {
         const void *yin = k == 1 ? x : (const char *)Y + (size_t)(k - 2) * a.blk * eb;
         void *yout = (char *)Y + (size_t)(k - 1) * a.blk * eb;
         void *args[] = {(void *)&a, (void *)&yin, (void *)&yout};
-        MPK_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kWaveThreads), args, 0, st));
+        MPK_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kSpmvThreads), args, 0, st));
     }
     return MPK_OK;
 }
@@ -617,10 +985,27 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
         const int32_t pw = std::min(pl->p, M - k0);
         if ((rc = epoch_guard(pl, st))) return rc;
         ca.e = exec_args(pl, nullptr, nullptr);
-        ca.e.p = pw;   // items of powers above pw are skipped
+        if (pw < pl->p) {   // a shorter last sweep has its own issue order
+            if (pl->rem_p != pw) {
+                std::vector<int32_t> work;
+                order_items(pl, pw, pl->lag, work);
+                if (pl->d_work_rem) {
+                    cudaStreamSynchronize(st);
+                    cudaFree(pl->d_work_rem);
+                    pl->d_work_rem = nullptr;
+                }
+                if ((rc = dev_alloc<int32_t>(nullptr, &pl->d_work_rem, work.size()))) return rc;
+                MPK_CUDA(cudaMemcpyAsync(pl->d_work_rem, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
+                MPK_CUDA(cudaStreamSynchronize(st));
+                pl->rem_p = pw;
+            }
+            ca.e.work = pl->d_work_rem;
+            ca.e.n_items = pl->n_tiles * pw;
+            ca.e.p = pw;
+        }
         ca.k0 = k0;
         void *args[] = {(void *)&ca};
-        MPK_CUDA(cudaLaunchKernel(pick_cheb(pl), dim3(pl->grid_ctas), dim3(kWaveThreads), args, 0, st));
+        if ((rc = launch_coop(pick_cheb(pl), pl->grid_ctas, pl->smem_bytes, args, st))) return rc;
     }
     if (!(flags & MPK_IO_PERMUTED)) {
         // acc (level order, n x 2 doubles) -> y (original order)

@@ -16,11 +16,16 @@ namespace mpk {
 constexpr int kChunk = 32;         // rows per SELL chunk = one warp, one row per lane
 constexpr int kMaxP = 255;         // powers are packed in 8 bits of a work item
 constexpr int kMaxNrhs = 64;
-constexpr int kWaveThreads = 256;  // threads of one wavefront CTA
+#ifndef MPK_COMPUTE_WARPS
+#define MPK_COMPUTE_WARPS 8
+#endif
+constexpr int kComputeWarps = MPK_COMPUTE_WARPS;         // warps that compute work items
+constexpr int kWaveThreads = (kComputeWarps + 1) * 32;   // plus one scheduler warp
+constexpr int kSpmvThreads = 256;                        // baseline SpMV CTA
 
 // Control words of a plan (device int32 array).
 enum Ctl : int {
-    CTL_NEXT = 0,       // next work item to hand out
+    CTL_UNUSED = 0,
     CTL_FINISHED = 1,   // CTAs that left the dispatch loop in this launch
     CTL_EPOCH = 2,      // epoch of the last completed launch (flags hold epochs)
     CTL_ABORT = 3,      // set when a wait expired: every CTA stops taking work
@@ -39,13 +44,21 @@ struct Plan {
     int32_t grid_ctas = 0, ctas_per_sm = 0;
     int32_t val_bytes = 8;
     int32_t has_diag = 0;           // diagonal stored apart (BF16 values)
-    double cache_bytes = 0, safety_f = 0.5, timeout_s = 2.0;
+    double cache_bytes = 0, safety_f = 0.5, timeout_s = 2.0, lag = -1.0, slope = 1.0;
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     int64_t packed_entries = 0, device_bytes = 0;
     double plan_ms = 0;
     uint64_t launches = 0;
     int32_t drop_tile = -1, drop_k = -1;   // one-shot test hook (mpk_plan_debug_drop_flag)
+    uint32_t tune = 0;              // MPK_TUNE_* bits
+    int32_t staged = 0;             // matrix slices staged in shared memory by bulk copies
+    int64_t stage_entries = 0;      // capacity of one stage in packed entries
+    size_t smem_bytes = 0;          // dynamic shared memory per wavefront CTA
+    // host copies kept to build the issue order of shorter sweeps
+    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_hi;
+    int32_t *d_work_rem = nullptr;  // issue order for rem_p powers (Chebyshev remainder sweep)
+    int32_t rem_p = 0;
 
     std::vector<int32_t> h_level_ptr, h_group_ptr;
 
@@ -55,13 +68,15 @@ struct Plan {
     int32_t *d_chunk_row = nullptr;    // n_chunks+1: first row of each chunk (sentinel n)
     int64_t *d_chunk_off = nullptr;    // n_chunks+1: first packed entry of each chunk
     int32_t *d_tile_chunk = nullptr;   // n_tiles+1: first chunk of each tile
+    int64_t *d_tile_off = nullptr;     // n_tiles+1: first packed entry of each tile
     int32_t *d_dep_lo = nullptr, *d_dep_hi = nullptr;  // n_tiles: tiles read at power k-1
     int32_t *d_work = nullptr;         // p*n_tiles items, (tile << 8) | power
     int32_t *d_pcol = nullptr;         // packed column indices, -1 = padding
     void *d_pval = nullptr;            // packed values (double / float / bf16)
     float *d_diag = nullptr;           // diagonal (only with has_diag)
     double *d_gersh = nullptr;         // Gershgorin row bounds scratch (lazily)
-    uint32_t *d_flags = nullptr;       // (p+1)*n_tiles completion epochs
+    uint32_t *d_flags = nullptr;       // (p+1) rows of fstride completion epochs
+    int32_t fstride = 0;               // flag row length: n_tiles rounded up to 4, plus 4
     int32_t *d_ctl = nullptr;          // CTL_WORDS control words
     void *d_io = nullptr;              // permuted copies for unpermuted I/O (lazily)
     size_t io_bytes = 0;
@@ -82,11 +97,15 @@ struct ExecArgs {
     uint32_t *flags;
     int32_t *ctl;
     int32_t n_tiles, n_items, n_chunks, nrhs, p;
+    int32_t fstride;        // flags of power k start at flags + k * fstride
     int64_t blk;            // elements of one vector block (n * nrhs)
     const void *x;          // y_0
     void *Y;                // p blocks
     uint64_t timeout_ns;
     int32_t drop_tile, drop_k;   // completion not published (test hook), -1 = none
+    const int64_t *tile_off;     // first packed entry of each tile
+    int64_t stage_entries;       // entries one shared-memory stage holds
+    uint32_t tune;               // MPK_TUNE_* bits
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).
@@ -134,6 +153,9 @@ int permute_vectors(Plan *pl, const void *src, void *dst, int32_t count, int32_t
                     int32_t to_level, cudaStream_t st);
 ExecArgs exec_args(const Plan *pl, const void *x, void *Y);
 int ensure_io(Plan *pl, size_t bytes);
+// Issue order of the (tile, power) items for powers 1..p_sweep (mpk_plan.cu).
+double order_items(const Plan *pl, int32_t p_sweep, double lag, std::vector<int32_t> &work);
+int wave_occupancy(const Plan *pl, int *ctas_per_sm);
 
 inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
 

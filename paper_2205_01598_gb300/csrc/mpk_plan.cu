@@ -10,7 +10,6 @@
 
 namespace mpk {
 
-int wave_occupancy(const Plan *pl, int *ctas_per_sm);   // mpk_exec.cu
 
 int cuda_status(cudaError_t e, const char *what, int line) {
     (void)cudaGetLastError();
@@ -470,6 +469,11 @@ __global__ void k_deps(int32_t n, const int32_t *prow, const int32_t *pcol, cons
     atomicMax(&hi[t], mx);
 }
 
+__global__ void k_tile_off(int32_t n_tiles, const int32_t *tile_chunk, const int64_t *chunk_off, int64_t *tile_off) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= n_tiles) tile_off[t] = chunk_off[tile_chunk[t]];
+}
+
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -499,7 +503,8 @@ struct Scratch {
 void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
-                  pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb};
+                  pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
+                  pl->d_tile_off, pl->d_work_rem};
     for (void *p : ps)
         if (p) cudaFree(p);
 }
@@ -673,10 +678,14 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     }
 
     // 8. tiles (work items) inside groups, chunks of 32 rows inside tiles
+    // Work items of 256 rows by default: small enough that the rows in flight
+    // (CTAs x tile rows) stay a small part of the level-group window, large
+    // enough to amortise the per-item dependency check; tiny matrices get
+    // smaller tiles so that every SM has work.
     int32_t tr = o->tile_rows;
     if (tr <= 0) {
-        int64_t target = (int64_t)n / ((int64_t)pl->num_sms * 8);
-        tr = (int32_t)std::min<int64_t>(1024, std::max<int64_t>(kChunk, (target / kChunk) * kChunk));
+        int64_t target = (int64_t)n / ((int64_t)pl->num_sms * 4);
+        tr = (int32_t)std::min<int64_t>(256, std::max<int64_t>(kChunk, (target / kChunk) * kChunk));
     }
     tr = std::max(kChunk, (tr / kChunk) * kChunk);
     pl->tile_rows = tr;
@@ -756,33 +765,51 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     k_deps<<<blocks_for(n, 256), 256, 0, st>>>(n, prow, pcol, tor, A->assume_symmetric ? 1 : 0, pl->d_dep_lo,
                                                pl->d_dep_hi);
 
-    // 11. work list in the diagonal order of the Lp diagram (Fig. 5) over level groups
+    // tile offsets into the packed arrays, and the shared-memory stage size
     {
-        const int32_t G = pl->n_groups;
+        MPK_TRY(dev_alloc(pl, &pl->d_tile_off, (size_t)pl->n_tiles + 1));
+        k_tile_off<<<blocks_for(pl->n_tiles + 1, 256), 256, 0, st>>>(pl->n_tiles, pl->d_tile_chunk, pl->d_chunk_off,
+                                                                    pl->d_tile_off);
+        std::vector<int64_t> toff((size_t)pl->n_tiles + 1);
+        MPK_CUDA(cudaMemcpyAsync(toff.data(), pl->d_tile_off, sizeof(int64_t) * toff.size(), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        int64_t mx = 0;
+        for (int32_t t = 0; t < pl->n_tiles; t++) mx = std::max(mx, toff[t + 1] - toff[t]);
+        pl->stage_entries = ((mx + kChunk - 1) / kChunk) * kChunk;
+        const size_t need = 2 * (size_t)pl->stage_entries * (size_t)(4 + pl->val_bytes);
+        pl->tune = o->tune;
+        pl->staged = !(o->tune & MPK_TUNE_NO_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
+        pl->smem_bytes = pl->staged ? need : 0;
+    }
+
+    // 11. grid size, then the work list: a skewed diagonal order of the Lp
+    //     diagram over level groups (see order_items)
+    int occ = 0;
+    MPK_TRY(wave_occupancy(pl, &occ));
+    int per_sm = o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : occ;
+    pl->ctas_per_sm = std::max(1, per_sm);
+    {
+        const int64_t items = (int64_t)pl->n_tiles * p;
+        pl->grid_ctas =
+            (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)pl->num_sms * pl->ctas_per_sm, items));
+        pl->h_dep_hi.resize((size_t)pl->n_tiles);
+        MPK_CUDA(cudaMemcpyAsync(pl->h_dep_hi.data(), pl->d_dep_hi, sizeof(int32_t) * pl->h_dep_hi.size(),
+                                 cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        pl->h_tile_row = tile_row;
+        pl->h_group_tile = group_tile;
         std::vector<int32_t> work;
-        work.reserve((size_t)pl->n_tiles * p);
-        for (int32_t d = 1; d <= G + p - 1; d++) {
-            int32_t k0 = std::max(1, d - G + 1), k1 = std::min(d, p);
-            for (int32_t k = k0; k <= k1; k++) {
-                int32_t g = d - k;
-                for (int32_t t = group_tile[g]; t < group_tile[g + 1]; t++) work.push_back((t << 8) | k);
-            }
-        }
+        pl->lag = o->lag;
+        pl->slope = order_items(pl, p, o->lag, work);
         MPK_TRY(dev_alloc(pl, &pl->d_work, work.size()));
         MPK_CUDA(cudaMemcpyAsync(pl->d_work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
         MPK_CUDA(cudaStreamSynchronize(st));
     }
-    MPK_TRY(dev_alloc(pl, &pl->d_flags, (size_t)(p + 1) * pl->n_tiles));
+    pl->fstride = ((pl->n_tiles + 3) / 4) * 4 + 4;
+    MPK_TRY(dev_alloc(pl, &pl->d_flags, (size_t)(p + 1) * pl->fstride));
     MPK_TRY(dev_alloc(pl, &pl->d_ctl, CTL_WORDS));
-    MPK_CUDA(cudaMemsetAsync(pl->d_flags, 0, sizeof(uint32_t) * (size_t)(p + 1) * pl->n_tiles, st));
+    MPK_CUDA(cudaMemsetAsync(pl->d_flags, 0, sizeof(uint32_t) * (size_t)(p + 1) * pl->fstride, st));
     MPK_CUDA(cudaMemsetAsync(pl->d_ctl, 0, sizeof(int32_t) * CTL_WORDS, st));
-
-    int occ = 0;
-    MPK_TRY(wave_occupancy(pl, &occ));
-    int per_sm = o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : std::min(occ, 4);
-    pl->ctas_per_sm = std::max(1, per_sm);
-    int64_t items = (int64_t)pl->n_tiles * p;
-    pl->grid_ctas = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)pl->num_sms * pl->ctas_per_sm, items));
 
     MPK_CUDA(cudaStreamSynchronize(st));
     MPK_CUDA(cudaGetLastError());
@@ -791,6 +818,51 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
 }
 
 }  // namespace
+
+// Issue order of the (tile, power) work items.  The Lp diagram of Fig. 5 is
+// traversed along diagonals: node (i, k) of level group i and power k sits on
+// diagonal i + k, and the paper visits a diagonal with k ascending, so node
+// (i, k) directly follows the node (i+1, k-1) it depends on (condition (C) of
+// Sec. 4.3).  A GPU runs hundreds of items at once, and that order would put
+// p dependent steps on every diagonal's critical path.  Items here are ordered
+// by the key v(t) + sigma * (k - 1), with v(t) the position of tile t in units
+// of level groups (group index plus the fraction of the group's rows before
+// the tile): the diagonals of the Lp diagram get slope sigma and the tiles of
+// the p nodes on a diagonal are interleaved.  sigma is the least slope that
+// puts every dependency (the tiles up to dep_hi[t] at power k-1) strictly
+// before its item, plus a lag that covers the items in flight, and at least 1
+// (the paper's slope, i.e. p+1 level groups between the first and last power
+// front, the working set Eq. 5 budgets for).  Ties go to the lower power, so
+// dependencies always come first and in-order hand-out cannot deadlock.
+double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &work) {
+    const std::vector<int32_t> &tile_row = pl->h_tile_row, &group_tile = pl->h_group_tile, &hi = pl->h_dep_hi;
+    const int32_t T = pl->n_tiles, G = pl->n_groups;
+    std::vector<double> v((size_t)T);
+    for (int32_t g = 0; g < G; g++) {
+        const double r0 = tile_row[group_tile[g]], r1 = tile_row[group_tile[g + 1]];
+        for (int32_t t = group_tile[g]; t < group_tile[g + 1]; t++) v[t] = g + (tile_row[t] - r0) / (r1 - r0);
+    }
+    double need = 0.0;
+    for (int32_t t = 0; t < T; t++) need = std::max(need, v[hi[t]] - v[t]);
+    if (lag < 0) {   // in-flight items measured in level groups per power front
+        const double tiles_per_group = (double)T / G;
+        lag = 1.5 * (double)pl->grid_ctas / ((double)p * tiles_per_group);
+    }
+    const double sigma = std::max(1.0, need + lag);
+    struct Item { double key; int32_t k, t; };
+    std::vector<Item> items;
+    items.reserve((size_t)T * p);
+    for (int32_t k = 1; k <= p; k++)
+        for (int32_t t = 0; t < T; t++) items.push_back({v[t] + sigma * (k - 1), k, t});
+    std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+        if (a.key != b.key) return a.key < b.key;
+        if (a.k != b.k) return a.k < b.k;
+        return a.t < b.t;
+    });
+    work.resize(items.size());
+    for (size_t i = 0; i < items.size(); i++) work[i] = (items[i].t << 8) | items[i].k;
+    return sigma;
+}
 
 int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st, int32_t *total) {
     return exclusive_scan<int32_t>(in, out, n, st, total);
@@ -817,6 +889,8 @@ int mpk_opts_default(mpk_opts *o) {
     o->ctas_per_sm = 0;
     o->timeout_s = 2.0;
     o->stream = nullptr;
+    o->lag = -1.0;
+    o->tune = 0;
     return MPK_OK;
 }
 
@@ -871,6 +945,9 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->device_bytes = pl.device_bytes + (int64_t)pl.io_bytes + (int64_t)pl.cheb_bytes;
     s->plan_ms = pl.plan_ms;
     s->cache_bytes = pl.cache_bytes;
+    s->slope = pl.slope;
+    s->staged = pl.staged;
+    s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
 }
 
