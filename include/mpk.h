@@ -57,12 +57,12 @@ typedef enum {
 typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
 
 /* Tuning bits of mpk_opts.tune (for autotuners; 0 = defaults).
- *  MPK_TUNE_NO_STAGE    read the matrix slices straight from global memory
- *                       instead of staging each work item's slice in shared
- *                       memory with bulk (TMA) copies.
- *  MPK_TUNE_EVICT_LAST  mark matrix slices evict-last in L2 until their last
- *                       power (they are always marked evict-first then).    */
-#define MPK_TUNE_NO_STAGE   1u
+ *  MPK_TUNE_STAGE       stage each work item's matrix slice in shared memory
+ *                       with bulk (TMA) copies, double-buffered, instead of
+ *                       reading it from global memory (used when it fits).
+ *  MPK_TUNE_EVICT_LAST  with staging: mark matrix slices evict-last in L2
+ *                       until their last power (always evict-first then).  */
+#define MPK_TUNE_STAGE      1u
 #define MPK_TUNE_EVICT_LAST 2u
 
 /* Flags of mpk_run / mpk_baseline_run / mpk_cheb. */

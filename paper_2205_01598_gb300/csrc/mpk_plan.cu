@@ -678,14 +678,14 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     }
 
     // 8. tiles (work items) inside groups, chunks of 32 rows inside tiles
-    // Work items of 256 rows by default: small enough that the rows in flight
+    // Work items of 512 rows by default: small enough that the rows in flight
     // (CTAs x tile rows) stay a small part of the level-group window, large
-    // enough to amortise the per-item dependency check; tiny matrices get
+    // enough to amortise the per-item synchronisation; tiny matrices get
     // smaller tiles so that every SM has work.
     int32_t tr = o->tile_rows;
     if (tr <= 0) {
         int64_t target = (int64_t)n / ((int64_t)pl->num_sms * 4);
-        tr = (int32_t)std::min<int64_t>(256, std::max<int64_t>(kChunk, (target / kChunk) * kChunk));
+        tr = (int32_t)std::min<int64_t>(512, std::max<int64_t>(kChunk, (target / kChunk) * kChunk));
     }
     tr = std::max(kChunk, (tr / kChunk) * kChunk);
     pl->tile_rows = tr;
@@ -778,7 +778,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         pl->stage_entries = ((mx + kChunk - 1) / kChunk) * kChunk;
         const size_t need = 2 * (size_t)pl->stage_entries * (size_t)(4 + pl->val_bytes);
         pl->tune = o->tune;
-        pl->staged = !(o->tune & MPK_TUNE_NO_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
+        pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
         pl->smem_bytes = pl->staged ? need : 0;
     }
 

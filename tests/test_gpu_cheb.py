@@ -57,3 +57,18 @@ def test_reduced_precision_cheb_error_bound(prec):
     err = _run(A, prec, 8, 64)
     print(prec, err)
     assert err <= 2e-5
+
+
+def test_staged_cheb_matches_oracle():
+    A = mi.anderson3d(12, W=16.5, seed=42)
+    plan = plan_of(A, 8, prec="f64", nrhs=2, tune=mpk.MPK_TUNE_STAGE)
+    assert mpk.mpk_plan_info(plan)["staged"] == 1
+    c, r = 0.5, 14.0
+    coef = oracle.cheb_coeffs_schroedinger(21, c, r, 2.0)
+    psi = mi.uniform(5, A.n) + 1j * mi.uniform(6, A.n)
+    ref = oracle.cheb(A, coef, c, r, psi)
+    xd = torch.from_numpy(np.stack([psi.real, psi.imag], 1).copy()).cuda()
+    yd = torch.empty(A.n, 2, dtype=torch.float64, device="cuda")
+    mpk.mpk_cheb(plan, coef, c, r, xd, yd)
+    y = yd.cpu().numpy()
+    assert np.max(np.abs(y[:, 0] + 1j * y[:, 1] - ref)) / np.max(np.abs(ref)) <= 1e-12

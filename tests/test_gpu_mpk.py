@@ -158,3 +158,19 @@ def test_config_3d_160_p8_full_size():
     assert np.all(rel_errors(got, ref[:, perm]) <= 1e-12)
     got32 = run_mpk(plan_of(A, p, prec="f32"), x[perm].astype(np.float32), permuted=True)
     assert np.all(rel_errors(got32, ref[:, perm]) <= 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16val"])
+@pytest.mark.parametrize("tile_rows", [128, 512])
+def test_staged_slices_match_oracle(prec, tile_rows):
+    """Opt-in form that stages each item's matrix slice in shared memory with
+    bulk copies (MPK_TUNE_STAGE, with the evict-last hint)."""
+    A = mi.anderson3d(18, seed=42) if prec == "bf16val" else mi.laplace3d(36)
+    p = 6
+    x = mi.random_vector(A.n, 21)
+    ref = oracle.mpk(A, x, p)
+    plan = plan_of(A, p, prec=prec, tile_rows=tile_rows, tune=mpk.MPK_TUNE_STAGE | mpk.MPK_TUNE_EVICT_LAST)
+    assert mpk.mpk_plan_info(plan)["staged"] == 1
+    xin = x if prec == "f64" else x.astype(np.float32)
+    err = rel_errors(run_mpk(plan, xin), ref)
+    assert np.all(err <= (1e-12 if prec == "f64" else 1e-5)), err
