@@ -214,6 +214,35 @@ int mpk_plan_destroy(mpk_plan_t plan);
  * cancels a pending drop.  MPK_ERR_INVALID for an item outside the plan.  */
 int mpk_plan_debug_drop_flag(mpk_plan_t plan, int32_t tile, int32_t power);
 
+/* Levels of Eq. 3 (the same values as mpk_plan_perm's level[] for a plan
+ * built with assume_symmetric != 0 and the same root) WITHOUT ANY DEVICE
+ * ALLOCATION.  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate device memory, for example code running
+ * inside a stream capture that is later replayed as a CUDA graph, or a host
+ * that pre-sizes all device memory at start-up and forbids allocation
+ * afterwards.  mpk_plan allocates, so such callers use this call.
+ *
+ * The scratch (frontier queue and control words) is a static device array
+ * inside this library, sized for n <= 1,048,576 vertices (about 4 MB, held
+ * on every GPU that loads the library until the process exits).  The caller
+ * passes the inputs and the output: n, nnz and the CRS arrays rowptr[n+1],
+ * col[nnz] (DEVICE, caller-owned; the stored pattern is taken as symmetric),
+ * the root, and level[n] (DEVICE, caller-allocated, overwritten).  *n_levels
+ * (host) receives L_m.  stream: cudaStream_t; timeout_s bounds each wait of
+ * the kernel (0 = 2 s).  The call synchronises the stream.
+ *
+ * The first call on a device looks up the device address of the array (and
+ * may load the library's device code), so make that first call before any
+ * stream capture.  Every call shares the one array and clears its control
+ * words on entry: calls that overlap on the GPU (other streams, other host
+ * threads) race and must not be issued.
+ *
+ * Errors: MPK_ERR_UNSUPPORTED if n > 1,048,576 (the scratch limit);
+ * MPK_ERR_INVALID for NULL pointers, n < 1, a root outside [0, n) or a
+ * malformed CRS (found on the device); MPK_ERR_TIMEOUT, MPK_ERR_CUDA.      */
+int mpk_levels_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, int32_t root,
+                       int32_t *level, int32_t *n_levels, void *stream, double timeout_s);
+
 /* Static description of a status code.                                     */
 const char *mpk_strerror(int status);
 

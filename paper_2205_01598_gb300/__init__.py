@@ -121,6 +121,7 @@ def load(path: str | None = None):
             "mpk_strerror": ([C.c_int], C.c_char_p),
             "mpk_plan_last_error": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
             "mpk_plan_debug_drop_flag": ([vp, i32, i32], C.c_int),
+            "mpk_levels_noalloc": ([i32, i64, vp, vp, i32, vp, C.POINTER(i32), vp, f64], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -275,6 +276,20 @@ def mpk_plan_last_error(plan: Plan):
 def mpk_plan_debug_drop_flag(plan: Plan, tile, power):
     """Test hook: the next wavefront launch does not publish item (tile, power)."""
     _check(load().mpk_plan_debug_drop_flag(plan.handle, int(tile), int(power)), "mpk_plan_debug_drop_flag")
+
+
+def mpk_levels_noalloc(rowptr, col, root=0, level=None, stream=None, timeout_s=2.0):
+    """Eq. 3 levels computed without any device allocation by the library
+    (mpk_levels_noalloc); returns (level tensor, number of levels).  Pass a
+    pre-allocated int32 `level` of length n so that nothing is allocated."""
+    import torch
+    n = rowptr.numel() - 1
+    if level is None:
+        level = torch.empty(n, dtype=torch.int32, device=rowptr.device)
+    nl = C.c_int32()
+    _check(load().mpk_levels_noalloc(n, col.numel(), _ptr(rowptr), _ptr(col), int(root), _ptr(level),
+                                     C.byref(nl), _stream(stream), float(timeout_s)), "mpk_levels_noalloc")
+    return level, nl.value
 
 
 def mpk_plan_destroy(plan: Plan):

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <climits>
 #include <cstring>
+#include <mutex>
 
 #include "mpk_internal.cuh"
 
@@ -817,6 +818,41 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     return MPK_OK;
 }
 
+// ---------------------------------------------------------------- allocation-free levels
+// Scratch of mpk_levels_noalloc: words [0, kStaticCtlWords) hold the control
+// block of the BFS kernel and the validation flag, the rest the frontier
+// queue.  It lives in the library's own device memory (reserved when the
+// module is loaded on a device and kept until the process exits).
+constexpr int32_t kStaticLevelsMaxN = 1 << 20;
+constexpr int32_t kStaticCtlWords = 64;
+constexpr int32_t kStaticBadWord = 32;
+static_assert(sizeof(BfsCtl) <= kStaticBadWord * sizeof(int32_t), "control block must fit");
+
+}  // namespace
+
+static __device__ __align__(256) int32_t g_levels_scratch[kStaticCtlWords + kStaticLevelsMaxN];
+
+namespace {
+
+std::mutex g_levels_scratch_mu;
+int32_t *g_levels_scratch_dev[256] = {};   // device address of the array, per device
+
+// Device address of the static scratch on the current device (looked up once).
+int static_levels_scratch(int32_t **out) {
+    int dev = 0;
+    MPK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return MPK_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_levels_scratch_mu);
+    if (!g_levels_scratch_dev[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_levels_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_levels_scratch)", __LINE__);
+        g_levels_scratch_dev[dev] = (int32_t *)ptr;
+    }
+    *out = g_levels_scratch_dev[dev];
+    return MPK_OK;
+}
+
 }  // namespace
 
 // Issue order of the (tile, power) work items.  The Lp diagram of Fig. 5 is
@@ -977,6 +1013,47 @@ const char *mpk_strerror(int status) {
     case MPK_ERR_UNSUPPORTED: return "unsupported request";
     default: return "unknown status";
     }
+}
+
+int mpk_levels_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, int32_t root,
+                       int32_t *level, int32_t *n_levels, void *stream, double timeout_s) {
+    if (!rowptr || !col || !level || !n_levels || n < 1 || nnz < 0 || nnz >= (int64_t)INT32_MAX) return MPK_ERR_INVALID;
+    if (root < 0 || root >= n) return MPK_ERR_INVALID;
+    if (n > kStaticLevelsMaxN) return MPK_ERR_UNSUPPORTED;   // beyond the static scratch
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *scratch = nullptr;
+    int rc = static_levels_scratch(&scratch);
+    if (rc) return rc;
+    BfsCtl *ctl = (BfsCtl *)scratch;
+    int32_t *bad = scratch + kStaticBadWord;
+    int32_t *queue = scratch + kStaticCtlWords;
+    // the array keeps the previous call's contents: clear what must start at zero
+    MPK_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * kStaticCtlWords, st));
+    MPK_CUDA(cudaMemsetAsync(level, 0xff, sizeof(int32_t) * (size_t)n, st));
+    k_validate<<<blocks_for((int64_t)n + 1, 256), 256, 0, st>>>(n, nnz, rowptr, col, bad);
+    MPK_CUDA(cudaGetLastError());
+    int32_t h_bad = 0;
+    MPK_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    if (h_bad) return MPK_ERR_INVALID;
+    int dev = 0, sms = 0, occ = 0;
+    MPK_CUDA(cudaGetDevice(&dev));
+    MPK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, 512, 0));
+    if (occ < 1) return MPK_ERR_CUDA;
+    int grid = sms * std::min(occ, 2);
+    const int32_t *no_trp = nullptr, *no_tcol = nullptr;
+    uint64_t tns = (uint64_t)((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
+    void *args[] = {(void *)&n, (void *)&rowptr, (void *)&col, (void *)&no_trp, (void *)&no_tcol, (void *)&root,
+                    (void *)&level, (void *)&queue, (void *)&ctl, (void *)&tns};
+    MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(grid), dim3(512), args, 0, st));
+    BfsCtl h_bc;
+    MPK_CUDA(cudaMemcpyAsync(&h_bc, ctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    if (h_bc.err) return h_bc.err;
+    if (h_bc.nlevels < 1 || h_bc.nlevels > n) return MPK_ERR_CUDA;
+    *n_levels = h_bc.nlevels;
+    return MPK_OK;
 }
 
 }  // extern "C"
