@@ -68,6 +68,8 @@ typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
 /* Flags of mpk_run / mpk_baseline_run / mpk_cheb. */
 #define MPK_IO_PERMUTED 1u  /* x and outputs are in the plan's level order   */
 #define MPK_ASYNC       2u  /* do not synchronise to read the device error word */
+#define MPK_SWEEP_ONE   4u  /* mpk_cheb: one power per launch (back-to-back SpMVs,
+                               the comparator of Sec. 7) instead of sweeps of p */
 
 /* A square sparse matrix in CRS form (Sec. 3.1, Fig. 1).  Device pointers,
  * caller-owned.  rowptr[n+1] (rowptr[0] = 0, non-decreasing, rowptr[n] = nnz),
@@ -189,7 +191,8 @@ int mpk_cheb_coeffs_schroedinger(int32_t M, double c, double r, double dt, doubl
  * have nrhs = 2: x and v_k are complex vectors stored as n x 2 (re, im) in
  * the plan precision (double for MPK_F64, float otherwise); y is n x 2
  * DOUBLE (the coefficient sum is accumulated in FP64).  coef: M+1 complex
- * numbers, interleaved, HOST memory.  Flags as for mpk_run.  Errors as for
+ * numbers, interleaved, HOST memory.  Flags as for mpk_run, plus
+ * MPK_SWEEP_ONE (same arithmetic, one power per launch).  Errors as for
  * mpk_run; MPK_ERR_INVALID if nrhs != 2, M < 1 or r == 0.                  */
 int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
              const void *x, double *y, uint32_t flags);

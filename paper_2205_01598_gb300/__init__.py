@@ -31,7 +31,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_CUDA, MPK_ERR_OOM, MPK_ERR_TIMEOUT, MPK_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 MPK_F64, MPK_F32, MPK_F32_BF16VAL = 0, 1, 2
-MPK_IO_PERMUTED, MPK_ASYNC = 1, 2
+MPK_IO_PERMUTED, MPK_ASYNC, MPK_SWEEP_ONE = 1, 2, 4
 MPK_TUNE_STAGE, MPK_TUNE_EVICT_LAST = 1, 2
 PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL}
 
@@ -252,14 +252,15 @@ def mpk_cheb_coeffs_schroedinger(M, c, r, dt) -> np.ndarray:
     return out[0::2] + 1j * out[1::2]
 
 
-def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False):
+def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False, one_power_per_launch=False):
     """y = sum_k coef_k T_k((A - c)/r) x (mpk_cheb); x: (n, 2) plan precision,
     y: (n, 2) float64 CUDA tensors; coef: complex host array of length M+1."""
     coef = np.asarray(coef, dtype=np.complex128)
     ci = np.empty(2 * coef.shape[0], dtype=np.float64)
     ci[0::2], ci[1::2] = coef.real, coef.imag
     _check(load().mpk_cheb(plan.handle, ci.ctypes.data_as(C.c_void_p), coef.shape[0] - 1, float(c), float(r),
-                           _ptr(x), _ptr(y), _flags(permuted, asynchronous)), "mpk_cheb")
+                           _ptr(x), _ptr(y),
+                           _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)), "mpk_cheb")
 
 
 def mpk_permute_vectors(plan: Plan, src, dst, count, to_level):

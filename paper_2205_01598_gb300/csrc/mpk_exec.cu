@@ -981,8 +981,9 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
     ca.coef = dcoef;
     ca.alpha = 1.0 / r;
     ca.beta = -c / r;
-    for (int32_t k0 = 0; k0 < M; k0 += pl->p) {
-        const int32_t pw = std::min(pl->p, M - k0);
+    const int32_t sweep = (flags & MPK_SWEEP_ONE) ? 1 : pl->p;
+    for (int32_t k0 = 0; k0 < M; k0 += sweep) {
+        const int32_t pw = std::min(sweep, M - k0);
         if ((rc = epoch_guard(pl, st))) return rc;
         ca.e = exec_args(pl, nullptr, nullptr);
         if (pw < pl->p) {   // a shorter last sweep has its own issue order

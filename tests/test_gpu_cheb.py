@@ -72,3 +72,21 @@ def test_staged_cheb_matches_oracle():
     mpk.mpk_cheb(plan, coef, c, r, xd, yd)
     y = yd.cpu().numpy()
     assert np.max(np.abs(y[:, 0] + 1j * y[:, 1] - ref)) / np.max(np.abs(ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16val"])
+def test_one_power_per_launch_is_bitwise_equal(prec):
+    """The back-to-back form (MPK_SWEEP_ONE) runs the same node arithmetic, so
+    it must reproduce the level-blocked sweeps bit for bit."""
+    A = mi.anderson3d(14, W=16.5, seed=42)
+    plan = plan_of(A, 8, prec=prec, nrhs=2)
+    c, r = 0.1, 14.25
+    coef = oracle.cheb_coeffs_schroedinger(30, c, r, 50.0 / r)
+    psi = mi.uniform(9, A.n) + 1j * mi.uniform(10, A.n)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    xd = torch.from_numpy(np.stack([psi.real, psi.imag], 1).copy()).to(dt).cuda()
+    y1 = torch.empty(A.n, 2, dtype=torch.float64, device="cuda")
+    y2 = torch.empty_like(y1)
+    mpk.mpk_cheb(plan, coef, c, r, xd, y1)
+    mpk.mpk_cheb(plan, coef, c, r, xd, y2, one_power_per_launch=True)
+    assert torch.equal(y1, y2)
