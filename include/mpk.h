@@ -197,6 +197,41 @@ int mpk_cheb_coeffs_schroedinger(int32_t M, double c, double r, double dt, doubl
 int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
              const void *x, double *y, uint32_t flags);
 
+/* ---------------------------------------------------------------- batches
+ * Several plans (different matrices, sizes, block widths nrhs and powers p)
+ * run in ONE persistent wavefront launch: their issue orders (each the
+ * diagonal order of its own Lp diagram) are merged by relative position, so
+ * every plan keeps its dependency order, and the items of all plans share
+ * the CTAs of the GPU.  Plans must have the same precision (MPK_F64 or
+ * MPK_F32; MPK_F32_BF16VAL is MPK_ERR_UNSUPPORTED) and device, and must not be
+ * run on their own while the batch runs (they share their dependency flags).
+ * The batch uses the stream of plans[0].  Vectors are in each plan's level
+ * order (as with MPK_IO_PERMUTED).                                          */
+typedef struct mpk_batch_s *mpk_batch_t;
+
+/* Builds the merged issue order of `count` plans (host array of handles,
+ * 1 <= count <= 1024; the batch keeps pointers to the plans, which must
+ * outlive it).                                                            */
+int mpk_batch_create(const mpk_plan_t *plans, int32_t count, mpk_batch_t *out);
+
+/* Number of work items and CTAs of the batched launch (host outputs).     */
+int mpk_batch_info(mpk_batch_t batch, int32_t *n_items, int32_t *grid_ctas);
+
+/* One launch: Ys[m][k-1] = A_m^k xs[m] for every plan m.  xs, Ys: HOST arrays
+ * of `count` DEVICE pointers (layouts as for mpk_run).  Errors as mpk_run.  */
+int mpk_batch_run(mpk_batch_t batch, const void *const *xs, void *const *Ys, uint32_t flags);
+
+/* Captures the batched launch for these xs / Ys into a CUDA graph (on a
+ * private stream) and keeps its executable instance in the batch.          */
+int mpk_batch_graph_capture(mpk_batch_t batch, const void *const *xs, void *const *Ys);
+
+/* Replays the captured graph on the batch's stream (MPK_ASYNC: no sync and
+ * no error read-back).  MPK_ERR_INVALID if nothing was captured.           */
+int mpk_batch_graph_launch(mpk_batch_t batch, uint32_t flags);
+
+/* Releases the batch (not its plans).  NULL is accepted.                   */
+int mpk_batch_destroy(mpk_batch_t batch);
+
 /* Reorders vectors between the caller's numbering and the plan's level
  * order (Sec. 4.5: the permutation vector recovers the original order).
  * src and dst: count blocks of n x nrhs elements of elem_bytes (4 or 8)

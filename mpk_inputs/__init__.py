@@ -250,3 +250,68 @@ def random_sparse(n: int, density: float, seed: int, symmetric: bool = True,
     if diag:
         np.fill_diagonal(A, np.diag(v))
     return from_dense(A, name=f"rand{'sym' if symmetric else ''}-{n}-{density}-{seed}")
+
+
+# ---------------------------------------------------------------- irregular graphs
+def zipf_degrees(n: int, seed: int, s: float = 2.0, base: int = 8, cap: int = 500) -> np.ndarray:
+    """Target degrees min(cap, base + Z), Z ~ Zipf(s) on 1..cap-base (finite
+    support, inverse-CDF sampling); mean about 12 for s = 2, base = 8."""
+    k = np.arange(1, cap - base + 1, dtype=np.float64)
+    cdf = np.cumsum(k ** -s)
+    cdf /= cdf[-1]
+    z = np.searchsorted(cdf, uniform01(seed, n), side="right") + 1
+    return np.minimum(cap, base + z).astype(np.int64)
+
+
+def zipf_graph(n: int, seed: int) -> CSR:
+    """Random symmetric sparse matrix with Zipf-distributed row degrees
+    (configuration model): half-edges are paired at random, self-loops and
+    duplicate pairs dropped; a_ij = a_ji ~ N(0,1) and a_ii = sum_j |a_ij| + 1
+    (diagonally dominant).  Rows come out with ascending columns.
+    Deterministic in (n, seed) (PCG64 of numpy for the pairing)."""
+    deg = zipf_degrees(n, seed)
+    half = np.repeat(np.arange(n, dtype=np.int64), deg)
+    if half.size % 2:
+        half = half[:-1]
+    half = np.random.default_rng(seed).permutation(half)
+    u, v = half[0::2], half[1::2]
+    keep = u != v
+    u, v = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
+    key = np.sort(u * n + v)                        # upper triangle, sorted by (row u, col v)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])]   # drop duplicate pairs
+    u, v = key // n, key % n
+    w = normal(seed + 2, u.size)
+    absw = np.abs(w)
+    lower_order = np.argsort(v * n + u)             # lower triangle entries (row v, col u) in row order
+    lu, lv, lw = v[lower_order], u[lower_order], w[lower_order]
+    cnt_up = np.bincount(u, minlength=n)
+    cnt_lo = np.bincount(lu, minlength=n)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt_lo + 1 + cnt_up, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    col = np.empty(nnz, dtype=np.int64)
+    val = np.empty(nnz, dtype=np.float64)
+    first_lo = np.concatenate([[0], np.cumsum(cnt_lo)[:-1]])
+    pos_lo = rowptr[:-1][lu] + (np.arange(lu.size) - first_lo[lu])
+    col[pos_lo], val[pos_lo] = lv, lw
+    pos_d = rowptr[:-1] + cnt_lo
+    col[pos_d] = np.arange(n)
+    val[pos_d] = np.bincount(u, absw, minlength=n) + np.bincount(v, absw, minlength=n) + 1.0
+    first_up = np.concatenate([[0], np.cumsum(cnt_up)[:-1]])
+    pos_up = pos_d[u] + 1 + (np.arange(u.size) - first_up[u])
+    col[pos_up], val[pos_up] = v, w
+    return CSR(n, rowptr, col, val, name=f"zipf-{n}-{seed}")
+
+
+def batch_workload(count: int = 64, seed0: int = 1000, n_lo: int = 20_000, n_hi: int = 2_000_000):
+    """The batched workload: `count` Zipf graphs, matrix m with seed seed0+m,
+    N ~ U[n_lo, n_hi], nrhs ~ U{1..16}, p ~ U{2..10}.  Returns a list of
+    (CSR, nrhs, p)."""
+    out = []
+    for m in range(count):
+        z = splitmix64(seed0 + m, 3)
+        n = n_lo + int(z[0] % np.uint64(n_hi - n_lo + 1))
+        nrhs = 1 + int(z[1] % np.uint64(16))
+        p = 2 + int(z[2] % np.uint64(9))
+        out.append((zipf_graph(n, seed0 + m), nrhs, p))
+    return out

@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
-SOURCES = ["mpk_plan.cu", "mpk_exec.cu"]
+SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -122,6 +122,12 @@ def load(path: str | None = None):
             "mpk_plan_last_error": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
             "mpk_plan_debug_drop_flag": ([vp, i32, i32], C.c_int),
             "mpk_levels_noalloc": ([i32, i64, vp, vp, i32, vp, C.POINTER(i32), vp, f64], C.c_int),
+            "mpk_batch_create": ([C.POINTER(vp), i32, C.POINTER(vp)], C.c_int),
+            "mpk_batch_info": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
+            "mpk_batch_run": ([vp, C.POINTER(vp), C.POINTER(vp), u32], C.c_int),
+            "mpk_batch_graph_capture": ([vp, C.POINTER(vp), C.POINTER(vp)], C.c_int),
+            "mpk_batch_graph_launch": ([vp, u32], C.c_int),
+            "mpk_batch_destroy": ([vp], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -291,6 +297,56 @@ def mpk_levels_noalloc(rowptr, col, root=0, level=None, stream=None, timeout_s=2
     _check(load().mpk_levels_noalloc(n, col.numel(), _ptr(rowptr), _ptr(col), int(root), _ptr(level),
                                      C.byref(nl), _stream(stream), float(timeout_s)), "mpk_levels_noalloc")
     return level, nl.value
+
+
+class Batch:
+    """Owner of an ``mpk_batch_t`` (keeps its plans alive)."""
+
+    def __init__(self, handle, plans):
+        self.handle, self.plans = handle, list(plans)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mpk_batch_destroy(self.handle)
+            self.handle = None
+
+
+def _ptr_array(tensors):
+    return (C.c_void_p * len(tensors))(*[_ptr(t).value for t in tensors])
+
+
+def mpk_batch_create(plans) -> Batch:
+    """One persistent launch for several plans (mpk_batch_create)."""
+    hs = (C.c_void_p * len(plans))(*[p.handle.value if isinstance(p.handle, C.c_void_p) else p.handle
+                                     for p in plans])
+    h = C.c_void_p()
+    _check(load().mpk_batch_create(hs, len(plans), C.byref(h)), "mpk_batch_create")
+    return Batch(h, plans)
+
+
+def mpk_batch_info(batch: Batch):
+    n, g = C.c_int32(), C.c_int32()
+    _check(load().mpk_batch_info(batch.handle, C.byref(n), C.byref(g)), "mpk_batch_info")
+    return {"n_items": n.value, "grid_ctas": g.value}
+
+
+def mpk_batch_run(batch: Batch, xs, Ys, asynchronous=False):
+    _check(load().mpk_batch_run(batch.handle, _ptr_array(xs), _ptr_array(Ys), MPK_ASYNC if asynchronous else 0),
+           "mpk_batch_run")
+
+
+def mpk_batch_graph_capture(batch: Batch, xs, Ys):
+    _check(load().mpk_batch_graph_capture(batch.handle, _ptr_array(xs), _ptr_array(Ys)), "mpk_batch_graph_capture")
+
+
+def mpk_batch_graph_launch(batch: Batch, asynchronous=False):
+    _check(load().mpk_batch_graph_launch(batch.handle, MPK_ASYNC if asynchronous else 0), "mpk_batch_graph_launch")
+
+
+def mpk_batch_destroy(batch: Batch):
+    if batch.handle:
+        _check(load().mpk_batch_destroy(batch.handle), "mpk_batch_destroy")
+        batch.handle = None
 
 
 def mpk_plan_destroy(plan: Plan):

@@ -364,16 +364,53 @@ constexpr int kBarDone = 2;    // compute warps -> scheduler: the current item i
 // form), starts the compute warps, and publishes the previous item with a
 // release store.  Its fences overlap the compute warps' work instead of
 // stalling them.
-template <typename Node, typename MT, bool STAGED, typename Extra>
-__device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra) {
+// Where the arguments and the epoch of a work item come from: one plan, or
+// one of the plans of a batch (per-item plan index, per-plan epoch).
+struct OnePlan {
+    const ExecArgs &a;
+    uint32_t epoch;
+    __device__ __forceinline__ int32_t plan_of(int32_t) const { return 0; }
+    __device__ __forceinline__ const ExecArgs &args(int32_t) const { return a; }
+    __device__ __forceinline__ uint32_t epoch_of(int32_t) const { return epoch; }
+    __device__ __forceinline__ void publish_epochs() const { atomicExch(a.ctl + CTL_EPOCH, (int)epoch); }
+};
+struct ManyPlans {
+    const ExecArgs *table;      // per plan (device memory)
+    const int32_t *wplan;       // plan of each work item
+    const uint32_t *epochs;     // per plan (shared memory)
+    int32_t *const *plan_ctl;   // control words of each plan (their epochs advance)
+    int32_t count;
+    __device__ __forceinline__ int32_t plan_of(int32_t j) const { return __ldg(wplan + j); }
+    __device__ __forceinline__ const ExecArgs &args(int32_t m) const { return table[m]; }
+    __device__ __forceinline__ uint32_t epoch_of(int32_t m) const { return epochs[m]; }
+    __device__ __forceinline__ void publish_epochs() const {
+        for (int32_t m = 0; m < count; m++) atomicExch(plan_ctl[m] + CTL_EPOCH, (int)epochs[m]);
+    }
+};
+
+// Persistent, warp-specialised wavefront.  Work items are dealt round-robin
+// in the issue order (item j goes to CTA j mod gridDim.x; each CTA runs its
+// items in order).  Every dependency of an item comes earlier in that order,
+// the launch is cooperative (all CTAs resident), and a CTA publishes a
+// finished item before it blocks on the dependencies of its next one, so the
+// lowest unfinished item can always run: the launch cannot deadlock.
+//
+// The last warp of the CTA schedules: it checks the dependencies of the next
+// item (flags loaded ahead of time), performs the acquire fence, has the
+// item's matrix slice copied into a shared-memory stage (bulk copy, staged
+// form), starts the compute warps, and publishes the previous item with a
+// release store.  Its fences overlap the compute warps' work instead of
+// stalling them.  `g` holds the launch-wide fields (issue order, control
+// words, limits); `src` the per-item plan arguments.
+template <typename Node, typename MT, bool STAGED, typename Src, typename Extra>
+__device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, const Extra &extra) {
     extern __shared__ __align__(128) unsigned char dsmem[];
-    __shared__ int s_item, s_stage;
+    __shared__ int s_item, s_stage, s_plan;
     __shared__ __align__(8) uint64_t mbar[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ncw = (int)(blockDim.x >> 5) - 1;
     const int nthr = (int)blockDim.x;
-    const uint32_t epoch = (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u;
-    const size_t stage_bytes = STAGED ? (size_t)a.stage_entries * (4 + sizeof(MT)) : 0;
+    const size_t stage_bytes = STAGED ? (size_t)g.stage_entries * (4 + sizeof(MT)) : 0;
     if (STAGED && threadIdx.x == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
@@ -387,50 +424,59 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra)
         int32_t issued[2] = {0, 0}, consumed[2] = {0, 0};   // bulk copies per stage
         auto issue = [&](int32_t jj, int st) {
             if (STAGED) {
-                if (lane == 0) stage_item<MT>(a, __ldg(a.work + jj), dsmem + st * stage_bytes, &mbar[st]);
+                if (lane == 0)
+                    stage_item<MT>(src.args(src.plan_of(jj)), __ldg(g.work + jj), dsmem + st * stage_bytes, &mbar[st]);
                 issued[st]++;
             }
         };
         FlagProbe pr;
         int32_t j = blockIdx.x;
-        bool ok = j < a.n_items;
+        bool ok = j < g.n_items;
+        int32_t m = 0;
         if (ok) {
             issue(j, 0);
-            if (j + G < a.n_items) issue(j + G, 1);
-            const int32_t wk = __ldg(a.work + j);
+            if (j + G < g.n_items) issue(j + G, 1);
+            const int32_t wk = __ldg(g.work + j);
+            m = src.plan_of(j);
             if ((wk & 255) > 1) {
-                pr.issue(a, wk >> 8, wk & 255, lane);
-                ok = wait_deps(a, pr, wk >> 8, wk & 255, epoch, lane);
+                const ExecArgs &aj = src.args(m);
+                pr.issue(aj, wk >> 8, wk & 255, lane);
+                ok = wait_deps(aj, pr, wk >> 8, wk & 255, src.epoch_of(m), lane);
             }
         }
         if (lane == 0) {
-            s_item = ok ? __ldg(a.work + j) : -1;
+            s_item = ok ? __ldg(g.work + j) : -1;
+            s_plan = m;
             s_stage = 0;
         }
         __syncwarp();
         named_arrive(kBarReady, nthr);
         int32_t i = 0;
         while (ok) {
-            const int32_t wk = __ldg(a.work + j);
+            const int32_t wk = __ldg(g.work + j);
             const int32_t jn = j + G;
-            int32_t wn = 0;
+            int32_t wn = 0, mn = 0;
             bool ready = true;
-            if (jn < a.n_items) {
-                wn = __ldg(a.work + jn);
+            if (jn < g.n_items) {
+                wn = __ldg(g.work + jn);
+                mn = src.plan_of(jn);
                 if ((wn & 255) > 1) {
-                    pr.issue(a, wn >> 8, wn & 255, lane);
-                    ready = pr.fits() ? pr.ready(epoch, lane) : ready_wide(a, wn >> 8, wn & 255, epoch, lane);
+                    const ExecArgs &an = src.args(mn);
+                    pr.issue(an, wn >> 8, wn & 255, lane);
+                    ready = pr.fits() ? pr.ready(src.epoch_of(mn), lane)
+                                      : ready_wide(an, wn >> 8, wn & 255, src.epoch_of(mn), lane);
                     if (ready) fence_acq_rel_gpu();
                 }
             }
             named_sync(kBarDone, nthr);   // compute warps finished item j
             if (STAGED) consumed[i & 1]++;
             auto publish = [&]() {
+                const ExecArgs &aj = src.args(m);
                 const int32_t t = wk >> 8, k = wk & 255;
-                if (lane == 0 && !(t == a.drop_tile && k == a.drop_k))
-                    st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
+                if (lane == 0 && !(t == aj.drop_tile && k == aj.drop_k))
+                    st_release_u32(aj.flags + (int64_t)k * aj.fstride + t, src.epoch_of(m));
             };
-            if (jn >= a.n_items) {
+            if (jn >= g.n_items) {
                 publish();
                 if (lane == 0) s_item = -1;
                 __syncwarp();
@@ -439,11 +485,12 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra)
             }
             if (!ready) {   // publish first, then block on the next item's dependencies
                 publish();
-                ready = wait_deps(a, pr, wn >> 8, wn & 255, epoch, lane);
+                ready = wait_deps(src.args(mn), pr, wn >> 8, wn & 255, src.epoch_of(mn), lane);
             }
-            if (ready && j + 2 * G < a.n_items) issue(j + 2 * G, i & 1);   // stage of item j is free
+            if (ready && j + 2 * G < g.n_items) issue(j + 2 * G, i & 1);   // stage of item j is free
             if (lane == 0) {
                 s_item = ready ? wn : -1;
+                s_plan = mn;
                 s_stage = (i + 1) & 1;
             }
             __syncwarp();
@@ -451,23 +498,24 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra)
             if (!ready) break;
             publish();   // off the compute warps' critical path (a repeat store is harmless)
             j = jn;
+            m = mn;
             i++;
         }
         // never leave with a bulk copy in flight (abort path)
         for (int st = 0; STAGED && st < 2; st++)
             while (consumed[st] < issued[st]) {
-                if (!mbar_wait(&mbar[st], (uint32_t)(consumed[st] & 1), a.timeout_ns) && lane == 0)
-                    record_timeout(a, 0, -1);
+                if (!mbar_wait(&mbar[st], (uint32_t)(consumed[st] & 1), g.timeout_ns) && lane == 0)
+                    record_timeout(g, 0, -1);
                 consumed[st]++;
             }
         __syncwarp();
         if (lane == 0) {
             __threadfence();
-            const int done = atomicAdd(a.ctl + CTL_FINISHED, 1);
-            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch, reset
-                atomicExch(a.ctl + CTL_FINISHED, 0);
-                atomicExch(a.ctl + CTL_ABORT, 0);
-                atomicExch(a.ctl + CTL_EPOCH, (int)epoch);
+            const int done = atomicAdd(g.ctl + CTL_FINISHED, 1);
+            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch(s), reset
+                atomicExch(g.ctl + CTL_FINISHED, 0);
+                atomicExch(g.ctl + CTL_ABORT, 0);
+                src.publish_epochs();
                 __threadfence();
             }
         }
@@ -478,19 +526,21 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra)
             named_sync(kBarReady, nthr);
             const int32_t wk = *(volatile int *)&s_item;
             const int st = *(volatile int *)&s_stage;
+            const int32_t m = *(volatile int *)&s_plan;
             if (wk < 0) break;
             const int32_t t = wk >> 8, k = wk & 255;
+            const ExecArgs &a = src.args(m);
             if (STAGED) {
-                const bool landed = mbar_wait(&mbar[st], st ? ph1 : ph0, a.timeout_ns);
+                const bool landed = mbar_wait(&mbar[st], st ? ph1 : ph0, g.timeout_ns);
                 if (st) ph1 ^= 1u; else ph0 ^= 1u;
                 if (!landed) {
-                    if (lane == 0) record_timeout(a, k, t);
+                    if (lane == 0) record_timeout(g, k, t);
                     named_arrive(kBarDone, nthr);
                     continue;
                 }
             }
             const MatView<MT, STAGED> mv{STAGED ? (const int32_t *)(dsmem + st * stage_bytes) : a.pcol,
-                                         STAGED ? (const MT *)(dsmem + st * stage_bytes + (size_t)a.stage_entries * 4)
+                                         STAGED ? (const MT *)(dsmem + st * stage_bytes + (size_t)g.stage_entries * 4)
                                                 : (const MT *)a.pval,
                                          STAGED ? __ldg(a.tile_off + t) : 0};
             Node::template run<STAGED>(a, mv, t, k, warp, ncw, lane, extra);
@@ -506,7 +556,8 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &a, const Extra &extra)
 #endif
 template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED>
 __global__ void MPK_WAVE_BOUNDS k_wave(ExecArgs a) {
-    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED, int>(a, 0);
+    const OnePlan src{a, (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u};
+    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED>(a, src, 0);
 }
 
 // Baseline: one SpMV over all chunks (warp per chunk, grid-stride).
@@ -591,7 +642,36 @@ struct ChebNode {
 
 template <typename VT, typename MT, bool DIAG, bool STAGED>
 __global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
-    wave_loop<ChebNode<VT, MT, DIAG>, MT, STAGED, ChebArgs>(ca.e, ca);
+    const OnePlan src{ca.e, (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u};
+    wave_loop<ChebNode<VT, MT, DIAG>, MT, STAGED>(ca.e, src, ca);
+}
+
+// ---------------------------------------------------------------- batched MPK
+// Plans of a batch may differ in block width and number of powers; the node
+// dispatches on the plan's nrhs.
+template <typename VT, typename MT>
+struct BatchNode {
+    template <bool STAGED>
+    __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t k,
+                                               int warp, int nwarps, int lane, const int &x) {
+        switch (a.nrhs) {
+        case 1: MpkNode<VT, MT, 1, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 2: MpkNode<VT, MT, 2, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 4: MpkNode<VT, MT, 4, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 8: MpkNode<VT, MT, 8, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        default: MpkNode<VT, MT, 8, false, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        }
+    }
+};
+
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kWaveThreads) k_batch_wave(BatchArgs b) {
+    __shared__ uint32_t s_epochs[kMaxBatch];
+    for (int32_t m = threadIdx.x; m < b.count; m += blockDim.x)
+        s_epochs[m] = (uint32_t)ld_relaxed_s32(b.plan_ctl[m] + CTL_EPOCH) + 1u;
+    __syncthreads();
+    const ManyPlans src{b.table, b.wplan, s_epochs, b.plan_ctl, b.count};
+    wave_loop<BatchNode<VT, MT>, MT, false>(b.g, src, 0);
 }
 
 // acc = coef_0 * v_0 (complex), v_0 = ring block 0
@@ -692,6 +772,15 @@ const void *pick_cheb_t(const Plan *pl) {
     return (const void *)k_cheb_wave<float, float, true, STAGED>;
 }
 const void *pick_wave(const Plan *pl) { return pl->staged ? pick_wave_t<true>(pl) : pick_wave_t<false>(pl); }
+
+}  // namespace
+
+const void *batch_kernel(int prec) {
+    return prec == MPK_F64 ? (const void *)k_batch_wave<double, double> : (const void *)k_batch_wave<float, float>;
+}
+
+namespace {
+
 const void *pick_cheb(const Plan *pl) { return pl->staged ? pick_cheb_t<true>(pl) : pick_cheb_t<false>(pl); }
 const void *pick_spmv(const Plan *pl) {
     if (pl->prec == MPK_F64) return spmv_ptr<double, double, false>(pl->nrhs);
@@ -752,7 +841,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
 
 // Cooperative launch (all CTAs co-resident), expressed with cudaLaunchKernelEx
 // so that it can also be captured in a CUDA graph.
-static int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st) {
+int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kWaveThreads);

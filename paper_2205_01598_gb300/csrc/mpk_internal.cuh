@@ -56,7 +56,7 @@ struct Plan {
     int64_t stage_entries = 0;      // capacity of one stage in packed entries
     size_t smem_bytes = 0;          // dynamic shared memory per wavefront CTA
     // host copies kept to build the issue order of shorter sweeps
-    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_hi;
+    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_hi, h_work;
     int32_t *d_work_rem = nullptr;  // issue order for rem_p powers (Chebyshev remainder sweep)
     int32_t rem_p = 0;
 
@@ -118,6 +118,16 @@ struct ChebArgs {
     int32_t k0;             // powers already computed before this sweep
 };
 
+// Launch-wide arguments of a batched wavefront (several plans, one launch).
+constexpr int kMaxBatch = 1024;
+struct BatchArgs {
+    ExecArgs g;                  // merged issue order, batch control words, limits
+    const ExecArgs *table;       // per plan
+    const int32_t *wplan;        // plan of each work item
+    int32_t *const *plan_ctl;    // control words of each plan
+    int32_t count;
+};
+
 // ---------------------------------------------------------------- host helpers
 int cuda_status(cudaError_t e, const char *what, int line);
 #define MPK_CUDA(call)                                                   \
@@ -156,6 +166,8 @@ int ensure_io(Plan *pl, size_t bytes);
 // Issue order of the (tile, power) items for powers 1..p_sweep (mpk_plan.cu).
 double order_items(const Plan *pl, int32_t p_sweep, double lag, std::vector<int32_t> &work);
 int wave_occupancy(const Plan *pl, int *ctas_per_sm);
+const void *batch_kernel(int prec);
+int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st);
 
 inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
 

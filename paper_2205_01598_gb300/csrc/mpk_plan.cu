@@ -805,6 +805,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         MPK_TRY(dev_alloc(pl, &pl->d_work, work.size()));
         MPK_CUDA(cudaMemcpyAsync(pl->d_work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
         MPK_CUDA(cudaStreamSynchronize(st));
+        pl->h_work = std::move(work);
     }
     pl->fstride = ((pl->n_tiles + 3) / 4) * 4 + 4;
     MPK_TRY(dev_alloc(pl, &pl->d_flags, (size_t)(p + 1) * pl->fstride));
