@@ -64,6 +64,9 @@ typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
  *                       until their last power (always evict-first then).  */
 #define MPK_TUNE_STAGE      1u
 #define MPK_TUNE_EVICT_LAST 2u
+#define MPK_TUNE_NO_SORT    4u  /* keep rows in level order inside a tile even
+                                   when sorting them by length (SELL-C-sigma,
+                                   sigma = tile rows) would cut the padding   */
 
 /* Flags of mpk_run / mpk_baseline_run / mpk_cheb. */
 #define MPK_IO_PERMUTED 1u  /* x and outputs are in the plan's level order   */
@@ -122,6 +125,7 @@ typedef struct {
     double slope;          /* sigma: level groups between consecutive power fronts */
     int32_t staged;        /* 1 if work items stage their slice in shared memory */
     int32_t smem_bytes;    /* dynamic shared memory per wavefront CTA            */
+    int32_t sorted;        /* 1 if rows are sorted by length inside each tile    */
 } mpk_plan_stats;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -135,7 +139,8 @@ int mpk_opts_default(mpk_opts *o);
  * vertices the lowest-numbered unvisited vertex starts the next level),
  * stable renumbering by (level, original index), the symmetric permutation
  * P A P^T, greedy level groups (Eq. 5, weight = stored entries x bytes per
- * entry of the chosen precision), the packed SELL-32 matrix and the
+ * entry of the chosen precision), the packed SELL-32 matrix (rows of a work
+ * item sorted by length when that cuts the padding by more than 10%) and the
  * dependency ranges of the wavefront.  1 <= p <= 255, 1 <= nrhs <= 64.
  * Errors: MPK_ERR_INVALID (NULL pointers, n < 1, p or nrhs out of range,
  * malformed CRS found on the device), MPK_ERR_OOM, MPK_ERR_CUDA.  On error

@@ -107,7 +107,7 @@ __device__ __forceinline__ void chunk_rows(const ExecArgs &a, const MatView<MT, 
     if (lane >= nrows) return;
     const int64_t off = __ldg(a.chunk_off + c);
     const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
-    const int32_t r = row0 + lane;
+    const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
     const int nrhs = EXACT ? W : a.nrhs;
     const int64_t e0 = off + lane;
     // B entries of the row are fetched together (indices and values first,
@@ -290,7 +290,7 @@ __device__ __forceinline__ void warp_chunks_staged(const ExecArgs &a, const MatV
                 const int32_t r0 = __ldg(a.chunk_row + c);
                 const int64_t off = __ldg(a.chunk_off + c);
                 if (lane < __ldg(a.chunk_row + c + 1) - r0) {
-                    row[i] = r0 + lane;
+                    row[i] = a.row_map ? __ldg(a.row_map + r0 + lane) : r0 + lane;
                     w[i] = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
                     e0[i] = off + lane;
                 }
@@ -595,7 +595,7 @@ struct ChebNode {
             if (lane >= nrows) continue;
             const int64_t off = __ldg(a.chunk_off + c);
             const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
-            const int32_t r = row0 + lane;
+            const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
             const int64_t e0 = off + lane;
             VT s0 = VT(0), s1 = VT(0);
             constexpr int B = 8;
@@ -696,7 +696,7 @@ __global__ void k_gersh(ExecArgs a, double *out) {
         if (lane < nrows) {
             const int64_t off = a.chunk_off[c];
             const int32_t wd = (int32_t)((a.chunk_off[c + 1] - off) / kChunk);
-            const int32_t r = row0 + lane;
+            const int32_t r = a.row_map ? a.row_map[row0 + lane] : row0 + lane;
             double d = a.diag ? (double)a.diag[r] : 0.0, s = 0.0;
             for (int32_t j = 0; j < wd; j++) {
                 int32_t col = a.pcol[off + (int64_t)j * kChunk + lane];
@@ -834,6 +834,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.drop_tile = -1;
     a.drop_k = -1;
     a.tile_off = pl->d_tile_off;
+    a.row_map = pl->d_row_map;
     a.stage_entries = pl->stage_entries;
     a.tune = pl->tune;
     return a;

@@ -53,6 +53,8 @@ struct Plan {
     int32_t drop_tile = -1, drop_k = -1;   // one-shot test hook (mpk_plan_debug_drop_flag)
     uint32_t tune = 0;              // MPK_TUNE_* bits
     int32_t staged = 0;             // matrix slices staged in shared memory by bulk copies
+    int32_t sorted = 0;             // rows of each tile packed in order of decreasing length
+    int32_t *d_row_map = nullptr;   // packed position -> row (only when sorted)
     int64_t stage_entries = 0;      // capacity of one stage in packed entries
     size_t smem_bytes = 0;          // dynamic shared memory per wavefront CTA
     // host copies kept to build the issue order of shorter sweeps
@@ -106,6 +108,7 @@ struct ExecArgs {
     const int64_t *tile_off;     // first packed entry of each tile
     int64_t stage_entries;       // entries one shared-memory stage holds
     uint32_t tune;               // MPK_TUNE_* bits
+    const int32_t *row_map;      // chunk position -> row (rows sorted by length in a tile); null = identity
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).

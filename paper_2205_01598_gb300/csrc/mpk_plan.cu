@@ -396,12 +396,35 @@ __device__ __forceinline__ int32_t packed_len(int32_t r, const int32_t *prow, co
     return len;
 }
 
-__global__ void k_chunk_width(int32_t n_chunks, const int32_t *chunk_row, const int32_t *prow, const int32_t *pcol,
-                              int split_diag, int64_t *cw) {
+__global__ void k_row_len(int32_t n, const int32_t *prow, const int32_t *pcol, int split_diag, int32_t *len) {
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) len[r] = packed_len(r, prow, pcol, split_diag);
+}
+
+// SELL-C-sigma with sigma = the tile: the rows of each tile are put in
+// order of decreasing packed length (ties: ascending row) so that a chunk
+// holds rows of similar length; row_map[position] = row.  One CTA per tile.
+__global__ void k_sort_tile_rows(int32_t n_tiles, const int32_t *tile_row, const int32_t *len, int32_t *row_map) {
+    extern __shared__ int32_t s_len[];
+    const int32_t t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const int32_t r0 = tile_row[t], nr = tile_row[t + 1] - r0;
+    for (int32_t i = threadIdx.x; i < nr; i += blockDim.x) s_len[i] = len[r0 + i];
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < nr; i += blockDim.x) {
+        const int32_t li = s_len[i];
+        int32_t rank = 0;
+        for (int32_t q = 0; q < nr; q++) rank += (s_len[q] > li) || (s_len[q] == li && q < i);
+        row_map[r0 + rank] = r0 + i;
+    }
+}
+
+__global__ void k_chunk_width(int32_t n_chunks, const int32_t *chunk_row, const int32_t *len, const int32_t *row_map,
+                              int64_t *cw) {
     int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chunks) return;
     int32_t w = 0;
-    for (int32_t r = chunk_row[c]; r < chunk_row[c + 1]; r++) w = max(w, packed_len(r, prow, pcol, split_diag));
+    for (int32_t q = chunk_row[c]; q < chunk_row[c + 1]; q++) w = max(w, len[row_map ? row_map[q] : q]);
     cw[c] = (int64_t)w * kChunk;
 }
 
@@ -415,17 +438,19 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_val<__nv_bfloat16>(doub
 
 // Column-major SELL-32: entry j of lane l of chunk c sits at off[c] + 32*j + l.
 template <typename MT>
-__global__ void k_pack(int32_t n_chunks, const int32_t *chunk_row, const int64_t *chunk_off, const int32_t *prow,
-                       const int32_t *pcol, const double *pval, int split_diag, int32_t *scol, MT *sval, float *diag) {
+__global__ void k_pack(int32_t n_chunks, const int32_t *chunk_row, const int64_t *chunk_off, const int32_t *row_map,
+                       const int32_t *prow, const int32_t *pcol, const double *pval, int split_diag, int32_t *scol,
+                       MT *sval, float *diag) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t c = (int32_t)(g / kChunk);
     int lane = (int)(g % kChunk);
     if (c >= n_chunks) return;
     int64_t off = chunk_off[c] + lane;
     int32_t w = (int32_t)((chunk_off[c + 1] - chunk_off[c]) / kChunk);
-    int32_t r = chunk_row[c] + lane;
+    const int32_t pos = chunk_row[c] + lane;
     int32_t j = 0;
-    if (r < chunk_row[c + 1]) {
+    if (pos < chunk_row[c + 1]) {
+        const int32_t r = row_map ? row_map[pos] : pos;
         double d = 0.0;
         for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
             if (split_diag && pcol[e] == r) { d += pval[e]; continue; }
@@ -470,6 +495,11 @@ __global__ void k_deps(int32_t n, const int32_t *prow, const int32_t *pcol, cons
     atomicMax(&hi[t], mx);
 }
 
+__global__ void k_widen(int32_t n, const int32_t *a, int64_t *b) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
 __global__ void k_tile_off(int32_t n_tiles, const int32_t *tile_chunk, const int64_t *chunk_off, int64_t *tile_off) {
     int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t <= n_tiles) tile_off[t] = chunk_off[tile_chunk[t]];
@@ -505,7 +535,7 @@ void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
                   pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
-                  pl->d_tile_off, pl->d_work_rem};
+                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map};
     for (void *p : ps)
         if (p) cudaFree(p);
 }
@@ -721,14 +751,34 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_CUDA(cudaMemcpyAsync(pl->d_group_ptr, pl->h_group_ptr.data(), pl->h_group_ptr.size() * 4,
                              cudaMemcpyHostToDevice, st));
 
-    // 9. packed SELL-32 matrix
+    // 9. packed SELL-32 matrix; rows of a tile sorted by length when that
+    //    removes more than a tenth of the padding (SELL-C-sigma, sigma = tile)
     int64_t *cw;
+    int32_t *rlen;
     MPK_TRY(S.alloc(&cw, (size_t)pl->n_chunks + 1));
+    MPK_TRY(S.alloc(&rlen, (size_t)n));
     MPK_CUDA(cudaMemsetAsync(cw + pl->n_chunks, 0, sizeof(int64_t), st));
-    k_chunk_width<<<blocks_for(pl->n_chunks, 256), 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, prow, pcol,
-                                                                split_diag, cw);
+    k_row_len<<<blocks_for(n, 256), 256, 0, st>>>(n, prow, pcol, split_diag, rlen);
+    k_chunk_width<<<blocks_for(pl->n_chunks, 256), 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, rlen, nullptr, cw);
     int64_t total = 0;
     MPK_TRY(exclusive_scan<int64_t>(cw, pl->d_chunk_off, (int64_t)pl->n_chunks + 1, st, &total));
+    {
+        int64_t stored = 0;
+        int64_t *d_len64;
+        MPK_TRY(S.alloc(&d_len64, (size_t)n + 1));
+        k_widen<<<blocks_for(n, 256), 256, 0, st>>>(n, rlen, d_len64);
+        MPK_CUDA(cudaMemsetAsync(d_len64 + n, 0, sizeof(int64_t), st));
+        MPK_TRY(exclusive_scan<int64_t>(d_len64, d_len64, (int64_t)n + 1, st, &stored));
+        if (!(o->tune & MPK_TUNE_NO_SORT) && tr <= 8192 && (double)total > 1.1 * (double)stored) {
+            MPK_TRY(dev_alloc(pl, &pl->d_row_map, (size_t)n));
+            const size_t sm = sizeof(int32_t) * (size_t)tr;
+            k_sort_tile_rows<<<pl->n_tiles, 256, sm, st>>>(pl->n_tiles, d_tile_row, rlen, pl->d_row_map);
+            k_chunk_width<<<blocks_for(pl->n_chunks, 256), 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, rlen,
+                                                                        pl->d_row_map, cw);
+            MPK_TRY(exclusive_scan<int64_t>(cw, pl->d_chunk_off, (int64_t)pl->n_chunks + 1, st, &total));
+            pl->sorted = 1;
+        }
+    }
     pl->packed_entries = total;
     MPK_TRY(dev_alloc(pl, &pl->d_pcol, (size_t)total));
     if (split_diag) MPK_TRY(dev_alloc(pl, &pl->d_diag, (size_t)n));
@@ -738,20 +788,20 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             double *v;
             MPK_TRY(dev_alloc(pl, &v, (size_t)total));
             pl->d_pval = v;
-            k_pack<double><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, prow, pcol, pval,
-                                                split_diag, pl->d_pcol, v, pl->d_diag);
+            k_pack<double><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, pl->d_row_map, prow,
+                                                pcol, pval, split_diag, pl->d_pcol, v, pl->d_diag);
         } else if (pl->val_bytes == 4) {
             float *v;
             MPK_TRY(dev_alloc(pl, &v, (size_t)total));
             pl->d_pval = v;
-            k_pack<float><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, prow, pcol, pval,
-                                               split_diag, pl->d_pcol, v, pl->d_diag);
+            k_pack<float><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, pl->d_row_map, prow,
+                                               pcol, pval, split_diag, pl->d_pcol, v, pl->d_diag);
         } else {
             __nv_bfloat16 *v;
             MPK_TRY(dev_alloc(pl, &v, (size_t)total));
             pl->d_pval = v;
-            k_pack<__nv_bfloat16><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, prow, pcol,
-                                                       pval, split_diag, pl->d_pcol, v, pl->d_diag);
+            k_pack<__nv_bfloat16><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, pl->d_row_map,
+                                                       prow, pcol, pval, split_diag, pl->d_pcol, v, pl->d_diag);
         }
     }
 
@@ -984,6 +1034,7 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->cache_bytes = pl.cache_bytes;
     s->slope = pl.slope;
     s->staged = pl.staged;
+    s->sorted = pl.sorted;
     s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
 }

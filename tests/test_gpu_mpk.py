@@ -174,3 +174,23 @@ def test_staged_slices_match_oracle(prec, tile_rows):
     xin = x if prec == "f64" else x.astype(np.float32)
     err = rel_errors(run_mpk(plan, xin), ref)
     assert np.all(err <= (1e-12 if prec == "f64" else 1e-5)), err
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_irregular_rows_sorted_by_length(prec, tol):
+    """Zipf-degree rows: the plan sorts rows by length inside each work item
+    (SELL-C-sigma); results match the oracle and, bit for bit, the unsorted
+    packing (the same entries are summed in the same order)."""
+    A = mi.zipf_graph(30000, 1003)
+    x = mi.random_vector(A.n, 8, 3)
+    ref = oracle.mpk(A, x, 5)
+    ps = plan_of(A, 5, prec=prec, nrhs=3, tile_rows=512)
+    pu = plan_of(A, 5, prec=prec, nrhs=3, tile_rows=512, tune=mpk.MPK_TUNE_NO_SORT)
+    i_s, i_u = mpk.mpk_plan_info(ps), mpk.mpk_plan_info(pu)
+    assert i_s["sorted"] == 1 and i_u["sorted"] == 0
+    assert i_s["packed_entries"] < 0.8 * i_u["packed_entries"]
+    xin = x if prec == "f64" else x.astype(np.float32)
+    ys = run_mpk(ps, xin)
+    assert np.all(rel_errors(ys, ref) <= tol)
+    assert np.array_equal(ys, run_mpk(pu, xin))
+    assert np.array_equal(ys, run_mpk(ps, xin, baseline=True))
