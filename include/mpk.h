@@ -150,6 +150,15 @@ int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out);
 /* Copies the plan summary to host memory *s.                              */
 int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s);
 
+/* Matrix features for the learned planner (computed on the GPU while the
+ * plan is built; HOST output out[count]): [0] log10 N, [1] mean and [2]
+ * standard deviation of the stored entries per row, [3] log10(1 + longest
+ * row), [4] mean and [5] maximum |column - row| / N of the level-ordered
+ * matrix, [6] log10 L_m, [7] largest level / N, [8] mean / largest level size,
+ * [9..24] share of the rows in each sixteenth of the level range.  Returns
+ * the number of features (25), or MPK_ERR_INVALID.                        */
+int mpk_plan_features(mpk_plan_t plan, float *out, int32_t count);
+
 /* Copies plan arrays to caller-allocated DEVICE buffers; any may be NULL.
  *  perm[n]        perm[new] = old (Sec. 4.5: recovers the original order)
  *  level_ptr[L+1] first new row of each level (Fig. 3e); level_ptr[L] = n
@@ -236,6 +245,63 @@ int mpk_batch_graph_launch(mpk_batch_t batch, uint32_t flags);
 
 /* Releases the batch (not its plans).  NULL is accepted.                   */
 int mpk_batch_destroy(mpk_batch_t batch);
+
+/* ---------------------------------------------------------------- tuning
+ * The parameters of the method (Sec. 5: the cache budget C of Eq. 5 through
+ * f, and how a power k is split into sweeps of p_m powers, Sec. 5.1) plus
+ * the GPU work-item size, searched by timing on the GPU.                    */
+typedef struct {
+    int32_t tile_rows;     /* in: rows per work item (0: automatic)           */
+    double safety_f;       /* in: f of Eq. 5 (with the base C)                */
+    uint32_t tune;         /* in: MPK_TUNE_* bits                             */
+    int32_t p_sweep;       /* in: powers per sweep (k = q*p_sweep + r: q
+                              sweeps of p_sweep powers and one of r)          */
+    double ms;             /* out: measured time of the k powers (ms), -1 if failed */
+    int32_t status;        /* out: mpk_status of planning / running           */
+} mpk_tune_candidate;
+
+/* Fills out[0..*count) with the default search grid for k powers: entry 0 is
+ * the library's default options (tile_rows 0, f 0.5, p_sweep k), then work
+ * items of 64/128/256/512/1024 rows x f in {0.25, 0.5} x p_sweep in {k,
+ * ceil(k/2) when k >= 4, 1 when k >= 2}.  MPK_ERR_INVALID if max is too small
+ * (count = entries written).                                                 */
+int mpk_tune_default_grid(int32_t k, mpk_tune_candidate *out, int32_t max, int32_t *count);
+
+/* Times every candidate for the MPK of A with k powers (opts from *base with
+ * the candidate's fields; each plan part run repeatedly until min_time_s),
+ * writes ms / status into cand[], and *best = the index of the fastest.
+ * Allocates temporary device vectors.  MPK_ERR_UNSUPPORTED if no candidate
+ * ran; MPK_ERR_CUDA ends the search.                                        */
+int mpk_autotune(const mpk_csr *A, int32_t k, const mpk_opts *base, double min_time_s, mpk_tune_candidate *cand,
+                 int32_t n_cand, int32_t *best);
+
+/* ---------------------------------------------------------------- planner network
+ * The multilayer perceptron of the learned planner (no counterpart in the
+ * paper; the paper tunes by search, Sec. 6.1): n_in -> n_hidden (ReLU) ->
+ * n_hidden (ReLU) -> n_out (linear), FP32, trained on the GPU with a masked
+ * mean-squared error sum_ij M_ij (Y_ij - T_ij)^2 / sum_ij M_ij and Adam.
+ * Parameters (flat, FP32): W1[n_hidden][n_in], b1, W2[n_hidden][n_hidden],
+ * b2, W3[n_out][n_hidden], b3; Glorot-uniform weights from SplitMix64(seed),
+ * zero biases.  X, T, M, Y are DEVICE row-major [batch][...] arrays.        */
+typedef struct mpk_mlp_s *mpk_mlp_t;
+
+int mpk_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void *stream, mpk_mlp_t *out);
+/* Number of parameters (or MPK_ERR_INVALID).                               */
+int32_t mpk_mlp_num_params(mpk_mlp_t net);
+/* Copy parameters to / from HOST memory (count must equal the number of
+ * parameters; setting also resets the Adam moments).                      */
+int mpk_mlp_get_params(mpk_mlp_t net, float *host, int32_t count);
+int mpk_mlp_set_params(mpk_mlp_t net, const float *host, int32_t count);
+/* Y[batch][n_out] = net(X[batch][n_in]).                                   */
+int mpk_mlp_forward(mpk_mlp_t net, const float *X, int32_t batch, float *Y);
+/* Loss (host *loss) and gradient of all parameters for one batch; the
+ * gradient stays on the device for mpk_mlp_adam_step and is copied to HOST
+ * grad_host[num_params] when that is not NULL.                             */
+int mpk_mlp_loss_grad(mpk_mlp_t net, const float *X, const float *T, const float *M, int32_t batch, double *loss,
+                      float *grad_host);
+/* One Adam update with the last gradient.                                  */
+int mpk_mlp_adam_step(mpk_mlp_t net, float lr, float beta1, float beta2, float eps);
+int mpk_mlp_destroy(mpk_mlp_t net);
 
 /* Reorders vectors between the caller's numbering and the plan's level
  * order (Sec. 4.5: the permutation vector recovers the original order).

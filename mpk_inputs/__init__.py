@@ -263,24 +263,11 @@ def zipf_degrees(n: int, seed: int, s: float = 2.0, base: int = 8, cap: int = 50
     return np.minimum(cap, base + z).astype(np.int64)
 
 
-def zipf_graph(n: int, seed: int) -> CSR:
-    """Random symmetric sparse matrix with Zipf-distributed row degrees
-    (configuration model): half-edges are paired at random, self-loops and
-    duplicate pairs dropped; a_ij = a_ji ~ N(0,1) and a_ii = sum_j |a_ij| + 1
-    (diagonally dominant).  Rows come out with ascending columns.
-    Deterministic in (n, seed) (PCG64 of numpy for the pairing)."""
-    deg = zipf_degrees(n, seed)
-    half = np.repeat(np.arange(n, dtype=np.int64), deg)
-    if half.size % 2:
-        half = half[:-1]
-    half = np.random.default_rng(seed).permutation(half)
-    u, v = half[0::2], half[1::2]
-    keep = u != v
-    u, v = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
-    key = np.sort(u * n + v)                        # upper triangle, sorted by (row u, col v)
-    key = key[np.concatenate([[True], key[1:] != key[:-1]])]   # drop duplicate pairs
-    u, v = key // n, key % n
-    w = normal(seed + 2, u.size)
+def _symmetric_from_pairs(n: int, u: np.ndarray, v: np.ndarray, wseed: int, name: str) -> CSR:
+    """Symmetric CRS from distinct upper-triangle pairs u < v sorted by (u, v):
+    a_uv = a_vu ~ N(0,1) from stream wseed, a_ii = sum_j |a_ij| + 1.  Rows come
+    out with ascending columns."""
+    w = normal(wseed, u.size)
     absw = np.abs(w)
     lower_order = np.argsort(v * n + u)             # lower triangle entries (row v, col u) in row order
     lu, lv, lw = v[lower_order], u[lower_order], w[lower_order]
@@ -300,7 +287,43 @@ def zipf_graph(n: int, seed: int) -> CSR:
     first_up = np.concatenate([[0], np.cumsum(cnt_up)[:-1]])
     pos_up = pos_d[u] + 1 + (np.arange(u.size) - first_up[u])
     col[pos_up], val[pos_up] = v, w
-    return CSR(n, rowptr, col, val, name=f"zipf-{n}-{seed}")
+    return CSR(n, rowptr, col, val, name=name)
+
+
+def zipf_graph(n: int, seed: int) -> CSR:
+    """Random symmetric sparse matrix with Zipf-distributed row degrees
+    (configuration model): half-edges are paired at random, self-loops and
+    duplicate pairs dropped; a_ij = a_ji ~ N(0,1) and a_ii = sum_j |a_ij| + 1
+    (diagonally dominant).  Rows come out with ascending columns.
+    Deterministic in (n, seed) (PCG64 of numpy for the pairing)."""
+    deg = zipf_degrees(n, seed)
+    half = np.repeat(np.arange(n, dtype=np.int64), deg)
+    if half.size % 2:
+        half = half[:-1]
+    half = np.random.default_rng(seed).permutation(half)
+    u, v = half[0::2], half[1::2]
+    keep = u != v
+    u, v = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
+    key = np.sort(u * n + v)                        # upper triangle, sorted by (row u, col v)
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])]   # drop duplicate pairs
+    return _symmetric_from_pairs(n, key // n, key % n, seed + 2, f"zipf-{n}-{seed}")
+
+
+def random_geometric_graph(n: int, dim: int, degree: float, seed: int) -> CSR:
+    """Random geometric graph as a symmetric matrix: n points uniform in the
+    unit cube [0,1)^dim (coordinates from SplitMix64 stream seed), an edge
+    between every pair closer than r, with r set so that an interior point has
+    `degree` neighbours on average (n * V_dim * r^dim = degree).  The points
+    are numbered in draw order, so the natural numbering has no locality;
+    values as in zipf_graph (stream seed + 1)."""
+    from scipy.spatial import cKDTree
+    vol = {2: np.pi, 3: 4.0 * np.pi / 3.0}[dim]
+    r = (degree / (n * vol)) ** (1.0 / dim)
+    pts = uniform01(seed, n * dim).reshape(n, dim)
+    pairs = cKDTree(pts).query_pairs(r, output_type="ndarray").astype(np.int64)
+    u, v = np.minimum(pairs[:, 0], pairs[:, 1]), np.maximum(pairs[:, 0], pairs[:, 1])
+    key = np.sort(u * n + v)
+    return _symmetric_from_pairs(n, key // n, key % n, seed + 1, f"rgg{dim}d-{n}-{seed}")
 
 
 def batch_workload(count: int = 64, seed0: int = 1000, n_lo: int = 20_000, n_hi: int = 2_000_000):

@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
-SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu"]
+SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -80,6 +80,11 @@ class mpk_opts(C.Structure):
                 ("lag", C.c_double), ("tune", C.c_uint32)]
 
 
+class mpk_tune_candidate(C.Structure):
+    _fields_ = [("tile_rows", C.c_int32), ("safety_f", C.c_double), ("tune", C.c_uint32), ("p_sweep", C.c_int32),
+                ("ms", C.c_double), ("status", C.c_int32)]
+
+
 class mpk_plan_stats(C.Structure):
     _fields_ = [("n", C.c_int32), ("p", C.c_int32), ("nrhs", C.c_int32), ("prec", C.c_int32),
                 ("nnz", C.c_int64), ("n_levels", C.c_int32), ("n_groups", C.c_int32),
@@ -122,6 +127,18 @@ def load(path: str | None = None):
             "mpk_plan_last_error": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], C.c_int),
             "mpk_plan_debug_drop_flag": ([vp, i32, i32], C.c_int),
             "mpk_levels_noalloc": ([i32, i64, vp, vp, i32, vp, C.POINTER(i32), vp, f64], C.c_int),
+            "mpk_plan_features": ([vp, vp, i32], C.c_int),
+            "mpk_mlp_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
+            "mpk_mlp_num_params": ([vp], C.c_int32),
+            "mpk_mlp_get_params": ([vp, vp, i32], C.c_int),
+            "mpk_mlp_set_params": ([vp, vp, i32], C.c_int),
+            "mpk_mlp_forward": ([vp, vp, i32, vp], C.c_int),
+            "mpk_mlp_loss_grad": ([vp, vp, vp, vp, i32, C.POINTER(f64), vp], C.c_int),
+            "mpk_mlp_adam_step": ([vp, C.c_float, C.c_float, C.c_float, C.c_float], C.c_int),
+            "mpk_mlp_destroy": ([vp], C.c_int),
+            "mpk_tune_default_grid": ([i32, C.POINTER(mpk_tune_candidate), i32, C.POINTER(i32)], C.c_int),
+            "mpk_autotune": ([C.POINTER(mpk_csr), i32, C.POINTER(mpk_opts), f64, C.POINTER(mpk_tune_candidate), i32,
+                              C.POINTER(i32)], C.c_int),
             "mpk_batch_create": ([C.POINTER(vp), i32, C.POINTER(vp)], C.c_int),
             "mpk_batch_info": ([vp, C.POINTER(i32), C.POINTER(i32)], C.c_int),
             "mpk_batch_run": ([vp, C.POINTER(vp), C.POINTER(vp), u32], C.c_int),
@@ -211,10 +228,50 @@ def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=
     return Plan(h, int(p), int(nrhs), o.prec, A.n, stream)
 
 
+def mpk_tune_default_grid(k):
+    """Default search grid of mpk_autotune for k powers: list of dicts."""
+    arr = (mpk_tune_candidate * 64)()
+    n = C.c_int32()
+    _check(load().mpk_tune_default_grid(int(k), arr, 64, C.byref(n)), "mpk_tune_default_grid")
+    return [{"tile_rows": arr[i].tile_rows, "safety_f": arr[i].safety_f, "tune": arr[i].tune,
+             "p_sweep": arr[i].p_sweep} for i in range(n.value)]
+
+
+def mpk_autotune(rowptr, col, val, k, candidates, *, prec="f64", nrhs=1, min_time_s=0.05, assume_symmetric=True,
+                 stream=None):
+    """Times each candidate (dicts with tile_rows, safety_f, tune, p_sweep) for
+    the MPK with k powers (mpk_autotune); returns (best index, list of ms
+    (-1 for failures))."""
+    lib = load()
+    A = mpk_csr(n=rowptr.numel() - 1, nnz=col.numel(), rowptr=_ptr(rowptr), col=_ptr(col), val=_ptr(val),
+                assume_symmetric=int(bool(assume_symmetric)))
+    o = mpk_opts_default()
+    o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    o.nrhs = int(nrhs)
+    o.stream = _stream(stream)
+    arr = (mpk_tune_candidate * len(candidates))()
+    for i, c in enumerate(candidates):
+        arr[i].tile_rows, arr[i].safety_f = int(c["tile_rows"]), float(c["safety_f"])
+        arr[i].tune, arr[i].p_sweep = int(c.get("tune", 0)), int(c["p_sweep"])
+    best = C.c_int32()
+    _check(lib.mpk_autotune(C.byref(A), int(k), C.byref(o), float(min_time_s), arr, len(candidates),
+                            C.byref(best)), "mpk_autotune")
+    return best.value, [arr[i].ms for i in range(len(candidates))]
+
+
 def mpk_plan_info(plan: Plan) -> dict:
     s = mpk_plan_stats()
     _check(load().mpk_plan_info(plan.handle, C.byref(s)), "mpk_plan_info")
     return {name: getattr(s, name) for name, _ in mpk_plan_stats._fields_}
+
+
+def mpk_plan_features(plan: Plan) -> np.ndarray:
+    """The 25 planner features of the plan's matrix (mpk_plan_features)."""
+    out = np.zeros(32, dtype=np.float32)
+    n = load().mpk_plan_features(plan.handle, out.ctypes.data_as(C.c_void_p), 32)
+    if n < 0:
+        _check(n, "mpk_plan_features")
+    return out[:n].copy()
 
 
 def mpk_plan_perm(plan: Plan):
@@ -347,6 +404,48 @@ def mpk_batch_destroy(batch: Batch):
     if batch.handle:
         _check(load().mpk_batch_destroy(batch.handle), "mpk_batch_destroy")
         batch.handle = None
+
+
+class Mlp:
+    """The planner's network (mpk_mlp_*): parameters and training on the GPU."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=7, stream=None):
+        self.shape = (int(n_in), int(n_hidden), int(n_out))
+        self.handle = C.c_void_p()
+        _check(load().mpk_mlp_create(self.shape[0], self.shape[1], self.shape[2], int(seed), _stream(stream),
+                                     C.byref(self.handle)), "mpk_mlp_create")
+        self.num_params = load().mpk_mlp_num_params(self.handle)
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(load().mpk_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p), self.num_params),
+               "mpk_mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().mpk_mlp_set_params(self.handle, p.ctypes.data_as(C.c_void_p), p.size), "mpk_mlp_set_params")
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty(X.shape[0], self.shape[2], dtype=torch.float32, device=X.device)
+        _check(load().mpk_mlp_forward(self.handle, _ptr(X), X.shape[0], _ptr(Y)), "mpk_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T, M, want_grad=False):
+        loss = C.c_double()
+        g = np.empty(self.num_params, dtype=np.float32) if want_grad else None
+        _check(load().mpk_mlp_loss_grad(self.handle, _ptr(X), _ptr(T), _ptr(M), X.shape[0], C.byref(loss),
+                                        g.ctypes.data_as(C.c_void_p) if want_grad else None), "mpk_mlp_loss_grad")
+        return (loss.value, g) if want_grad else loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(load().mpk_mlp_adam_step(self.handle, lr, beta1, beta2, eps), "mpk_mlp_adam_step")
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mpk_mlp_destroy(self.handle)
+            self.handle = None
 
 
 def mpk_plan_destroy(plan: Plan):

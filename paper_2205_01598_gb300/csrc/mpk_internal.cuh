@@ -49,6 +49,8 @@ struct Plan {
     int device = 0, num_sms = 0;
     int64_t packed_entries = 0, device_bytes = 0;
     double plan_ms = 0;
+    static constexpr int kFeatures = 25;   // matrix features for the learned planner
+    float features[kFeatures] = {};
     uint64_t launches = 0;
     int32_t drop_tile = -1, drop_k = -1;   // one-shot test hook (mpk_plan_debug_drop_flag)
     uint32_t tune = 0;              // MPK_TUNE_* bits

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -368,6 +369,40 @@ __global__ void k_perm_fill(int32_t n, const int32_t *rp, const int32_t *col, co
     }
 }
 
+// Row statistics of P A P^T for the planner's features: sum and sum of
+// squares of row lengths, the longest row, and the sum / maximum of the
+// distance |column - row| (bandwidth of the level-ordered matrix).
+__global__ void k_row_stats(int32_t n, const int32_t *prow, const int32_t *pcol, unsigned long long *acc) {
+    __shared__ unsigned long long s[5];
+    if (threadIdx.x < 5) s[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long len_sum = 0, len_sq = 0, len_max = 0, dist_sum = 0, dist_max = 0;
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const unsigned long long len = (unsigned long long)(prow[r + 1] - prow[r]);
+        len_sum += len;
+        len_sq += len * len;
+        len_max = len > len_max ? len : len_max;
+        for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
+            const unsigned long long d = (unsigned long long)abs(pcol[e] - r);
+            dist_sum += d;
+            dist_max = d > dist_max ? d : dist_max;
+        }
+    }
+    atomicAdd(&s[0], len_sum);
+    atomicAdd(&s[1], len_sq);
+    atomicMax(&s[2], len_max);
+    atomicAdd(&s[3], dist_sum);
+    atomicMax(&s[4], dist_max);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&acc[0], s[0]);
+        atomicAdd(&acc[1], s[1]);
+        atomicMax(&acc[2], s[2]);
+        atomicAdd(&acc[3], s[3]);
+        atomicMax(&acc[4], s[4]);
+    }
+}
+
 __global__ void k_level_nnz(int32_t nlevels, const int32_t *level_ptr, const int32_t *prow, int64_t *lnnz) {
     int32_t l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l < nlevels) lnnz[l] = (int64_t)prow[level_ptr[l + 1]] - prow[level_ptr[l]];
@@ -655,6 +690,27 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     k_perm_fill<<<blocks_for(n, 128), 128, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm, pl->d_iperm, prow,
                                                     pcol, pval);
 
+    // features of the matrix for the learned planner (host array of the plan)
+    {
+        unsigned long long *d_acc;
+        MPK_TRY(S.alloc(&d_acc, 5));
+        MPK_CUDA(cudaMemsetAsync(d_acc, 0, 5 * sizeof(unsigned long long), st));
+        k_row_stats<<<std::min<unsigned>(blocks_for(n, 256), (unsigned)pl->num_sms * 8), 256, 0, st>>>(n, prow, pcol,
+                                                                                                      d_acc);
+        unsigned long long h[5];
+        MPK_CUDA(cudaMemcpyAsync(h, d_acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        const double N = (double)n, mean = (double)h[0] / N;
+        const double var = std::max(0.0, (double)h[1] / N - mean * mean);
+        float *f = pl->features;
+        f[0] = (float)std::log10(N);
+        f[1] = (float)mean;
+        f[2] = (float)std::sqrt(var);
+        f[3] = (float)std::log10(1.0 + (double)h[2]);
+        f[4] = (float)((double)h[3] / std::max(1.0, (double)h[0]) / N);   // mean |col-row| / N
+        f[5] = (float)((double)h[4] / N);                                  // max |col-row| / N
+    }
+
     // 6. level sizes to the host
     int64_t *d_lnnz;
     MPK_TRY(S.alloc(&d_lnnz, (size_t)L));
@@ -686,6 +742,17 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_CUDA(cudaStreamSynchronize(st));
     for (int32_t l = 0; l < L; l++)
         pl->max_level_rows = std::max(pl->max_level_rows, pl->h_level_ptr[l + 1] - pl->h_level_ptr[l]);
+    {   // level features: count, largest level, and the share of rows in each
+        // sixteenth of the level range (shape of the level-size profile)
+        float *f = pl->features;
+        f[6] = (float)std::log10((double)L);
+        f[7] = (float)((double)pl->max_level_rows / n);
+        f[8] = (float)((double)n / L / std::max(1, pl->max_level_rows));   // mean / largest level size
+        for (int q = 0; q < 16; q++) {
+            const int32_t l0 = (int32_t)((int64_t)L * q / 16), l1 = (int32_t)((int64_t)L * (q + 1) / 16);
+            f[9 + q] = (float)((double)(pl->h_level_ptr[l1] - pl->h_level_ptr[l0]) / n);
+        }
+    }
 
     // 7. level groups (Eq. 5): add levels while (p+1) * weight(T) < f * C
     {
@@ -1037,6 +1104,12 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->sorted = pl.sorted;
     s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
+}
+
+int mpk_plan_features(mpk_plan_t plan, float *out, int32_t count) {
+    if (!plan || !out || count < 1) return MPK_ERR_INVALID;
+    for (int32_t i = 0; i < count; i++) out[i] = i < Plan::kFeatures ? plan->pl.features[i] : 0.0f;
+    return Plan::kFeatures;
 }
 
 int mpk_plan_perm(mpk_plan_t plan, int32_t *perm, int32_t *level_ptr, int32_t *group_ptr, int32_t *level) {
