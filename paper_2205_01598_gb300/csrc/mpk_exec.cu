@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <type_traits>
+
 #include "mpk_internal.cuh"
 
 // Compile-time tuning of the wavefront kernels: entries of a row fetched per
@@ -324,9 +326,133 @@ __device__ __forceinline__ void warp_chunks_staged(const ExecArgs &a, const MatV
     }
 }
 
+// ---------------------------------------------------------------- register-held slices
+// A compute warp handles chunks c0 + warp + i*ncw of a work item's tile.  The
+// first kPC of them -- chunk record, row, and the first kPE entries of the
+// lane's row -- are loaded into registers one work item ahead.  Those loads
+// read only the matrix, never a vector, so they are issued before the item's
+// dependencies are known to be complete; once the item is released only the
+// gathers of the input vector remain on its critical path.
+#ifndef MPK_PIPE_CHUNKS
+#define MPK_PIPE_CHUNKS 2
+#endif
+#ifndef MPK_PIPE_ENTRIES
+#define MPK_PIPE_ENTRIES 8
+#endif
+constexpr int kPC = MPK_PIPE_CHUNKS;    // chunks of a warp held in registers
+constexpr int kPE = MPK_PIPE_ENTRIES;   // entries of a row held in registers
+
+template <typename MT>
+struct Slice {
+    int4 rec[kPC];           // {first row, rows, first entry / 32, width}; rows 0 = no chunk
+    int32_t row[kPC];        // output row of this lane, -1 = none
+    int32_t col[kPC][kPE];   // -1 = past the row's end
+    MT val[kPC][kPE];
+    int32_t c0, c1;          // chunk range of the item's tile
+};
+
+__device__ __forceinline__ void slice_recs(const ExecArgs &a, int32_t c0, int32_t c1, int warp, int ncw,
+                                           int4 (&rec)[kPC]) {
+#pragma unroll
+    for (int i = 0; i < kPC; i++) {
+        const int32_t c = c0 + warp + i * ncw;
+        rec[i] = c < c1 ? __ldg(a.chunk_rec + c) : make_int4(0, 0, 0, 0);
+    }
+}
+
+template <typename MT>
+__device__ __forceinline__ void slice_entries(const ExecArgs &a, Slice<MT> &s, int lane) {
+#pragma unroll
+    for (int i = 0; i < kPC; i++) {
+        const int4 r = s.rec[i];
+        const bool on = lane < r.y;
+        s.row[i] = on ? (a.row_map ? __ldg(a.row_map + r.x + lane) : r.x + lane) : -1;
+        const int64_t e0 = (int64_t)r.z * kChunk + lane;
+#pragma unroll
+        for (int u = 0; u < kPE; u++) {
+            const bool in = on && u < r.w;
+            s.col[i][u] = in ? __ldg(a.pcol + e0 + (int64_t)u * kChunk) : -1;
+            s.val[i][u] = in ? __ldg((const MT *)a.pval + e0 + (int64_t)u * kChunk) : MT{};
+        }
+    }
+}
+
+// acc[i][q] = sum over the entries of the lane's row in held chunk i of
+// value * yin[col * G + q], in entry order (the order of chunk_rows, so both
+// paths round alike).  All gathers of the held entries are issued first.
+template <typename VT, typename MT, int G>
+__device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT> &s, const VT *yin, int lane,
+                                          VT (&acc)[kPC][G]) {
+    VT g[kPC][kPE][G];
+#pragma unroll
+    for (int i = 0; i < kPC; i++)
+#pragma unroll
+        for (int u = 0; u < kPE; u++)
+#pragma unroll
+            for (int q = 0; q < G; q++) g[i][u][q] = s.col[i][u] >= 0 ? yin[(int64_t)s.col[i][u] * G + q] : VT(0);
+#pragma unroll
+    for (int i = 0; i < kPC; i++)
+#pragma unroll
+        for (int q = 0; q < G; q++) acc[i][q] = VT(0);
+#pragma unroll
+    for (int i = 0; i < kPC; i++)
+#pragma unroll
+        for (int u = 0; u < kPE; u++)
+            if (s.col[i][u] >= 0) {
+                const VT v = to_vt<MT, VT>(s.val[i][u]);
+#pragma unroll
+                for (int q = 0; q < G; q++) acc[i][q] = fma(v, g[i][u][q], acc[i][q]);
+            }
+    // entries past the held ones (rows wider than kPE)
+#pragma unroll
+    for (int i = 0; i < kPC; i++) {
+        const int32_t w = s.rec[i].w;
+        if (s.row[i] < 0 || w <= kPE) continue;
+        const int64_t e0 = (int64_t)s.rec[i].z * kChunk + lane;
+        constexpr int B = 8;
+        for (int32_t j0 = kPE; j0 < w; j0 += B) {
+            int32_t cols[B];
+            VT vals[B];
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const bool in = j0 + u < w;
+                cols[u] = in ? __ldg(a.pcol + e0 + (int64_t)(j0 + u) * kChunk) : -1;
+                vals[u] = in ? to_vt<MT, VT>(__ldg((const MT *)a.pval + e0 + (int64_t)(j0 + u) * kChunk)) : VT(0);
+            }
+#pragma unroll
+            for (int u = 0; u < B; u++)
+                if (cols[u] >= 0)
+#pragma unroll
+                    for (int q = 0; q < G; q++) acc[i][q] = fma(vals[u], yin[(int64_t)cols[u] * G + q], acc[i][q]);
+        }
+    }
+}
+
 // Body of one work item (tile t, power k) of the plain MPK.
 template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
 struct MpkNode {
+    static constexpr bool kPipe = W == 1 && EXACT;   // single vectors run from register-held slices
+
+    template <typename Extra>
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT> &s, int32_t t, int32_t k,
+                                                    int warp, int nwarps, int lane, const Extra &) {
+        const VT *yin = k == 1 ? (const VT *)a.x : (const VT *)a.Y + (int64_t)(k - 2) * a.blk;
+        VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
+        VT acc[kPC][1];
+        slice_sum<VT, MT, 1>(a, s, yin, lane, acc);
+#pragma unroll
+        for (int i = 0; i < kPC; i++) {
+            const int32_t r = s.row[i];
+            if (r < 0) continue;
+            VT v = acc[i][0];
+            if (DIAG) v = fma((VT)__ldg(a.diag + r), yin[r], v);
+            yout[r] = v;
+        }
+        const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
+        for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps)
+            chunk_rows<VT, MT, 1, true, DIAG, false>(a, mv, c, lane, yin, yout);
+    }
+
     template <bool STAGED>
     __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t k,
                                                int warp, int nwarps, int lane, const int &) {
@@ -351,19 +477,6 @@ __device__ __forceinline__ void named_arrive(int id, int nthreads) {
 constexpr int kBarReady = 1;   // scheduler -> compute warps: the next item may start
 constexpr int kBarDone = 2;    // compute warps -> scheduler: the current item is finished
 
-// Persistent, warp-specialised wavefront.  Work items are dealt round-robin
-// in the issue order (item j goes to CTA j mod gridDim.x; each CTA runs its
-// items in order).  Every dependency of an item comes earlier in that order,
-// the launch is cooperative (all CTAs resident), and a CTA publishes a
-// finished item before it blocks on the dependencies of its next one, so the
-// lowest unfinished item can always run: the launch cannot deadlock.
-//
-// The last warp of the CTA schedules: it checks the dependencies of the next
-// item (flags loaded ahead of time), performs the acquire fence, has the
-// item's matrix slice copied into a shared-memory stage (bulk copy, staged
-// form), starts the compute warps, and publishes the previous item with a
-// release store.  Its fences overlap the compute warps' work instead of
-// stalling them.
 // Where the arguments and the epoch of a work item come from: one plan, or
 // one of the plans of a batch (per-item plan index, per-plan epoch).
 struct OnePlan {
@@ -402,6 +515,11 @@ struct ManyPlans {
 // release store.  Its fences overlap the compute warps' work instead of
 // stalling them.  `g` holds the launch-wide fields (issue order, control
 // words, limits); `src` the per-item plan arguments.
+//
+// With one plan and no stage, the compute warps hold the next item's matrix
+// slice in registers (Slice): they know which item comes next because the
+// dealing is static -- the scheduler hands them items blockIdx.x,
+// blockIdx.x + gridDim.x, ... in that order, or -1 to stop.
 template <typename Node, typename MT, bool STAGED, typename Src, typename Extra>
 __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, const Extra &extra) {
     extern __shared__ __align__(128) unsigned char dsmem[];
@@ -519,6 +637,44 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
                 __threadfence();
             }
         }
+    } else if constexpr (!STAGED && Node::kPipe && std::is_same<Src, OnePlan>::value) {
+        // ------------------------------------------------------------ compute warps, register-held slices
+        const ExecArgs &a = src.args(0);
+        const int64_t G = gridDim.x;
+        int64_t j = blockIdx.x;
+        auto range = [&](int64_t jj, int32_t &c0, int32_t &c1) {
+            c0 = c1 = 0;
+            if (jj < g.n_items) {
+                const int32_t t = __ldg(g.work + jj) >> 8;
+                c0 = __ldg(a.tile_chunk + t);
+                c1 = __ldg(a.tile_chunk + t + 1);
+            }
+        };
+        Slice<MT> s;
+        range(j, s.c0, s.c1);
+        slice_recs(a, s.c0, s.c1, warp, ncw, s.rec);
+        slice_entries(a, s, lane);
+        int32_t n0, n1;   // chunk range of item j + G
+        range(j + G, n0, n1);
+        for (;;) {
+            named_sync(kBarReady, nthr);
+            const int32_t wk = *(volatile int *)&s_item;
+            if (wk < 0) break;
+            int4 rn[kPC];   // records of item j + G, and the chunk range of item j + 2G
+            slice_recs(a, n0, n1, warp, ncw, rn);
+            int32_t m0, m1;
+            range(j + 2 * G, m0, m1);
+            Node::pipe_run(a, s, wk >> 8, wk & 255, warp, ncw, lane, extra);
+            s.c0 = n0;
+            s.c1 = n1;
+#pragma unroll
+            for (int i = 0; i < kPC; i++) s.rec[i] = rn[i];
+            slice_entries(a, s, lane);   // item j + G, used after its release
+            n0 = m0;
+            n1 = m1;
+            j += G;
+            named_arrive(kBarDone, nthr);
+        }
     } else {
         // ------------------------------------------------------------ compute warps
         uint32_t ph0 = 0, ph1 = 0;
@@ -579,64 +735,97 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(ExecArgs a, const VT *yin
 // the coefficient sum are done in FP64.
 template <typename VT, typename MT, bool DIAG>
 struct ChebNode {
+    static constexpr bool kPipe = true;
+
+    struct Vecs {
+        const VT *yin, *yprev;
+        VT *yout;
+        double cre, cim;
+        int32_t k;
+    };
+    __device__ __forceinline__ static Vecs vecs(const ExecArgs &a, const ChebArgs &ca, int32_t j) {
+        const int32_t k = ca.k0 + j;
+        VT *ring = (VT *)ca.ring;
+        return Vecs{ring + (int64_t)((k - 1) % 3) * a.blk, ring + (int64_t)((k + 1) % 3) * a.blk,   // (k-2) mod 3
+                    ring + (int64_t)(k % 3) * a.blk, ca.coef[2 * k], ca.coef[2 * k + 1], k};
+    }
+
+    // Row r of the sweep step, given (s0, s1) = (A v_{k-1})[r] without a
+    // separately stored diagonal.
+    __device__ __forceinline__ static void row_out(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
+                                                   VT s0, VT s1) {
+        const double u0 = (double)v.yin[2 * (int64_t)r], u1 = (double)v.yin[2 * (int64_t)r + 1];
+        double a0, a1;
+        if (DIAG) {   // the diagonal term enters in FP64 together with the shift
+            const double d = (double)__ldg(a.diag + r);
+            a0 = ca.alpha * ((double)s0 + d * u0) + ca.beta * u0;
+            a1 = ca.alpha * ((double)s1 + d * u1) + ca.beta * u1;
+        } else {
+            a0 = ca.alpha * (double)s0 + ca.beta * u0;
+            a1 = ca.alpha * (double)s1 + ca.beta * u1;
+        }
+        double n0 = a0, n1 = a1;
+        if (v.k > 1) {
+            n0 = 2.0 * a0 - (double)v.yprev[2 * (int64_t)r];
+            n1 = 2.0 * a1 - (double)v.yprev[2 * (int64_t)r + 1];
+        }
+        v.yout[2 * (int64_t)r] = (VT)n0;
+        v.yout[2 * (int64_t)r + 1] = (VT)n1;
+        double *acc = ca.acc + 2 * (int64_t)r;
+        acc[0] += v.cre * n0 - v.cim * n1;
+        acc[1] += v.cre * n1 + v.cim * n0;
+    }
+
+    template <bool STAGED>
+    __device__ __forceinline__ static void chunk(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t c, int lane,
+                                                 const ChebArgs &ca, const Vecs &v) {
+        const int32_t row0 = __ldg(a.chunk_row + c);
+        const int32_t nrows = __ldg(a.chunk_row + c + 1) - row0;
+        if (lane >= nrows) return;
+        const int64_t off = __ldg(a.chunk_off + c);
+        const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
+        const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
+        const int64_t e0 = off + lane;
+        VT s0 = VT(0), s1 = VT(0);
+        constexpr int B = 8;
+        for (int32_t q0 = 0; q0 < w; q0 += B) {
+            int32_t cols[B];
+            VT vals[B];
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const bool in = q0 + u < w;
+                cols[u] = in ? mv.c(e0 + (int64_t)(q0 + u) * kChunk) : -1;
+                vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(q0 + u) * kChunk)) : VT(0);
+            }
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                if (cols[u] >= 0) {
+                    s0 = fma(vals[u], v.yin[2 * (int64_t)cols[u]], s0);
+                    s1 = fma(vals[u], v.yin[2 * (int64_t)cols[u] + 1], s1);
+                }
+            }
+        }
+        row_out(a, ca, v, r, s0, s1);
+    }
+
     template <bool STAGED>
     __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t j,
                                                int warp, int nwarps, int lane, const ChebArgs &ca) {
-        const int32_t k = ca.k0 + j;
-        VT *ring = (VT *)ca.ring;
-        const VT *yin = ring + (int64_t)((k - 1) % 3) * a.blk;
-        const VT *yprev = ring + (int64_t)((k + 1) % 3) * a.blk;   // (k-2) mod 3
-        VT *yout = ring + (int64_t)(k % 3) * a.blk;
-        const double cre = ca.coef[2 * k], cim = ca.coef[2 * k + 1];
+        const Vecs v = vecs(a, ca, j);
         const int32_t c1 = __ldg(a.tile_chunk + t + 1);
-        for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps) {
-            const int32_t row0 = __ldg(a.chunk_row + c);
-            const int32_t nrows = __ldg(a.chunk_row + c + 1) - row0;
-            if (lane >= nrows) continue;
-            const int64_t off = __ldg(a.chunk_off + c);
-            const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
-            const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
-            const int64_t e0 = off + lane;
-            VT s0 = VT(0), s1 = VT(0);
-            constexpr int B = 8;
-            for (int32_t q0 = 0; q0 < w; q0 += B) {
-                int32_t cols[B];
-                VT vals[B];
+        for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps) chunk<STAGED>(a, mv, c, lane, ca, v);
+    }
+
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT> &s, int32_t t, int32_t j,
+                                                    int warp, int nwarps, int lane, const ChebArgs &ca) {
+        const Vecs v = vecs(a, ca, j);
+        VT acc[kPC][2];
+        slice_sum<VT, MT, 2>(a, s, v.yin, lane, acc);
 #pragma unroll
-                for (int u = 0; u < B; u++) {
-                    const bool in = q0 + u < w;
-                    cols[u] = in ? mv.c(e0 + (int64_t)(q0 + u) * kChunk) : -1;
-                    vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(q0 + u) * kChunk)) : VT(0);
-                }
-#pragma unroll
-                for (int u = 0; u < B; u++) {
-                    if (cols[u] >= 0) {
-                        s0 = fma(vals[u], yin[2 * (int64_t)cols[u]], s0);
-                        s1 = fma(vals[u], yin[2 * (int64_t)cols[u] + 1], s1);
-                    }
-                }
-            }
-            const double u0 = (double)yin[2 * (int64_t)r], u1 = (double)yin[2 * (int64_t)r + 1];
-            double a0, a1;
-            if (DIAG) {   // the diagonal term enters in FP64 together with the shift
-                const double d = (double)__ldg(a.diag + r);
-                a0 = ca.alpha * ((double)s0 + d * u0) + ca.beta * u0;
-                a1 = ca.alpha * ((double)s1 + d * u1) + ca.beta * u1;
-            } else {
-                a0 = ca.alpha * (double)s0 + ca.beta * u0;
-                a1 = ca.alpha * (double)s1 + ca.beta * u1;
-            }
-            double n0 = a0, n1 = a1;
-            if (k > 1) {
-                n0 = 2.0 * a0 - (double)yprev[2 * (int64_t)r];
-                n1 = 2.0 * a1 - (double)yprev[2 * (int64_t)r + 1];
-            }
-            yout[2 * (int64_t)r] = (VT)n0;
-            yout[2 * (int64_t)r + 1] = (VT)n1;
-            double *acc = ca.acc + 2 * (int64_t)r;
-            acc[0] += cre * n0 - cim * n1;
-            acc[1] += cre * n1 + cim * n0;
-        }
+        for (int i = 0; i < kPC; i++)
+            if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i][0], acc[i][1]);
+        const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
+        for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
     }
 };
 
@@ -651,6 +840,11 @@ __global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
 // dispatches on the plan's nrhs.
 template <typename VT, typename MT>
 struct BatchNode {
+    static constexpr bool kPipe = false;
+    template <typename Extra>
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &, const Slice<MT> &, int32_t, int32_t, int, int,
+                                                    int, const Extra &) {}
+
     template <bool STAGED>
     __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t k,
                                                int warp, int nwarps, int lane, const int &x) {
@@ -835,6 +1029,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.drop_k = -1;
     a.tile_off = pl->d_tile_off;
     a.row_map = pl->d_row_map;
+    a.chunk_rec = pl->d_chunk_rec;
     a.stage_entries = pl->stage_entries;
     a.tune = pl->tune;
     return a;

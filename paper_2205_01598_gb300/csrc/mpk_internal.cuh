@@ -71,6 +71,7 @@ struct Plan {
     int32_t *d_level_ptr = nullptr, *d_group_ptr = nullptr;
     int32_t *d_chunk_row = nullptr;    // n_chunks+1: first row of each chunk (sentinel n)
     int64_t *d_chunk_off = nullptr;    // n_chunks+1: first packed entry of each chunk
+    int4 *d_chunk_rec = nullptr;       // n_chunks: {first row, rows, first entry / 32, width}
     int32_t *d_tile_chunk = nullptr;   // n_tiles+1: first chunk of each tile
     int64_t *d_tile_off = nullptr;     // n_tiles+1: first packed entry of each tile
     int32_t *d_dep_lo = nullptr, *d_dep_hi = nullptr;  // n_tiles: tiles read at power k-1
@@ -111,6 +112,7 @@ struct ExecArgs {
     int64_t stage_entries;       // entries one shared-memory stage holds
     uint32_t tune;               // MPK_TUNE_* bits
     const int32_t *row_map;      // chunk position -> row (rows sorted by length in a tile); null = identity
+    const int4 *chunk_rec;       // per chunk {first row, rows, first entry / 32, width}
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).

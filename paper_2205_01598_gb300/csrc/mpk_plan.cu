@@ -540,6 +540,16 @@ __global__ void k_tile_off(int32_t n_tiles, const int32_t *tile_chunk, const int
     if (t <= n_tiles) tile_off[t] = chunk_off[tile_chunk[t]];
 }
 
+// Chunk records {first row, rows, first packed entry / 32, width}: the four
+// facts a warp needs about a chunk, in one 16-byte load.
+__global__ void k_chunk_rec(int32_t n_chunks, const int32_t *chunk_row, const int64_t *chunk_off, int4 *rec) {
+    int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
+    const int32_t r0 = chunk_row[c];
+    const int64_t o0 = chunk_off[c];
+    rec[c] = make_int4(r0, chunk_row[c + 1] - r0, (int32_t)(o0 / kChunk), (int32_t)((chunk_off[c + 1] - o0) / kChunk));
+}
+
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -570,7 +580,7 @@ void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
                   pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
-                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map};
+                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec};
     for (void *p : ps)
         if (p) cudaFree(p);
 }
@@ -847,6 +857,10 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         }
     }
     pl->packed_entries = total;
+    if (total / kChunk >= (int64_t)INT32_MAX) return MPK_ERR_UNSUPPORTED;   // chunk records hold offset / 32
+    MPK_TRY(dev_alloc(pl, &pl->d_chunk_rec, (size_t)pl->n_chunks));
+    k_chunk_rec<<<blocks_for(pl->n_chunks, 256), 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off,
+                                                              pl->d_chunk_rec);
     MPK_TRY(dev_alloc(pl, &pl->d_pcol, (size_t)total));
     if (split_diag) MPK_TRY(dev_alloc(pl, &pl->d_diag, (size_t)n));
     {
