@@ -67,6 +67,18 @@ typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
 #define MPK_TUNE_NO_SORT    4u  /* keep rows in level order inside a tile even
                                    when sorting them by length (SELL-C-sigma,
                                    sigma = tile rows) would cut the padding   */
+/*  MPK_TUNE_RESIDENT    each CTA owns a work item's tile for all p powers:
+ *                       the tile's packed slice is copied into shared memory
+ *                       once (bulk copies, two stages) and every power reads
+ *                       it there, so the matrix leaves HBM once per sweep and
+ *                       L2 carries only the vectors.  Tiles are sized to the
+ *                       stage (tile_rows 0) and 1 or 2 CTAs run per SM
+ *                       (ctas_per_sm).  Used when nrhs is 1 or 2, the stages
+ *                       fit, and the grid exceeds (p-1) times the widest
+ *                       forward dependency span in tiles (which rules out a
+ *                       cycle of waits); otherwise the plan keeps the
+ *                       work-list schedule (mpk_plan_stats.resident = 0).   */
+#define MPK_TUNE_RESIDENT   8u
 
 /* Flags of mpk_run / mpk_baseline_run / mpk_cheb. */
 #define MPK_IO_PERMUTED 1u  /* x and outputs are in the plan's level order   */
@@ -126,6 +138,8 @@ typedef struct {
     int32_t staged;        /* 1 if work items stage their slice in shared memory */
     int32_t smem_bytes;    /* dynamic shared memory per wavefront CTA            */
     int32_t sorted;        /* 1 if rows are sorted by length inside each tile    */
+    int32_t resident;      /* 1 if the plan runs the resident schedule           */
+    int32_t dep_span;      /* widest forward dependency span, in tiles          */
 } mpk_plan_stats;
 
 typedef struct mpk_plan_s *mpk_plan_t;

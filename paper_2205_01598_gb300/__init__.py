@@ -32,7 +32,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_CUDA, MPK_ERR_OOM, MPK_ERR_TIMEOUT, MPK_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 MPK_F64, MPK_F32, MPK_F32_BF16VAL = 0, 1, 2
 MPK_IO_PERMUTED, MPK_ASYNC, MPK_SWEEP_ONE = 1, 2, 4
-MPK_TUNE_STAGE, MPK_TUNE_EVICT_LAST, MPK_TUNE_NO_SORT = 1, 2, 4
+MPK_TUNE_STAGE, MPK_TUNE_EVICT_LAST, MPK_TUNE_NO_SORT, MPK_TUNE_RESIDENT = 1, 2, 4, 8
 PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL}
 
 
@@ -92,7 +92,8 @@ class mpk_plan_stats(C.Structure):
                 ("grid_ctas", C.c_int32), ("val_bytes", C.c_int32), ("packed_entries", C.c_int64),
                 ("matrix_bytes", C.c_int64), ("device_bytes", C.c_int64), ("plan_ms", C.c_double),
                 ("cache_bytes", C.c_double), ("slope", C.c_double), ("staged", C.c_int32),
-                ("smem_bytes", C.c_int32), ("sorted", C.c_int32)]
+                ("smem_bytes", C.c_int32), ("sorted", C.c_int32), ("resident", C.c_int32),
+                ("dep_span", C.c_int32)]
 
 
 _lib = None

@@ -186,7 +186,9 @@ struct FlagProbe {
         }
     }
     __device__ __forceinline__ bool fits() const { return hi - base < kProbeVec * 128; }
-    __device__ __forceinline__ bool ready(uint32_t epoch, int lane) const {
+    // `skip`: a tile whose flag need not be read (the caller's own tile at
+    // the previous power, finished by the same CTA), -1 for none.
+    __device__ __forceinline__ bool ready(uint32_t epoch, int lane, int32_t skip = -1) const {
         bool good = true;
 #pragma unroll
         for (int q = 0; q < kProbeVec; q++) {
@@ -194,18 +196,18 @@ struct FlagProbe {
             const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
 #pragma unroll
             for (int s = 0; s < 4; s++)
-                if (i + s >= lo && i + s <= hi) good &= (w[s] == epoch);
+                if (i + s >= lo && i + s <= hi && i + s != skip) good &= (w[s] == epoch);
         }
         return __all_sync(0xffffffffu, good);
     }
 };
 
 // Bounded check for a range wider than one probe (huge levels, small tiles).
-__device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch, int lane) {
+__device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch, int lane, int32_t skip = -1) {
     const uint32_t *f = a.flags + (int64_t)(k - 1) * a.fstride;
     const int32_t lo = __ldg(a.dep_lo + t), hi = __ldg(a.dep_hi + t);
     bool ok = true;
-    for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (ld_relaxed_u32(f + i) == epoch);
+    for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
     return __all_sync(0xffffffffu, ok);
 }
 
@@ -220,9 +222,10 @@ __device__ void record_timeout(const ExecArgs &a, int32_t k, int32_t t) {
 // Polls until the item's dependencies are complete.  Bounded: after
 // timeout_ns it records MPK_ERR_TIMEOUT with the node, raises the abort word
 // and returns false; it also returns false once another CTA has aborted.
-__device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k, uint32_t epoch, int lane) {
+__device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k, uint32_t epoch, int lane,
+                          int32_t skip = -1) {
     const bool wide = !pr.fits();
-    if (wide ? ready_wide(a, t, k, epoch, lane) : pr.ready(epoch, lane)) {
+    if (wide ? ready_wide(a, t, k, epoch, lane, skip) : pr.ready(epoch, lane, skip)) {
         fence_acq_rel_gpu();
         return true;
     }
@@ -242,10 +245,10 @@ __device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
         if (wide) {
-            if (ready_wide(a, t, k, epoch, lane)) break;
+            if (ready_wide(a, t, k, epoch, lane, skip)) break;
         } else {
             pr.issue(a, t, k, lane);
-            if (pr.ready(epoch, lane)) break;
+            if (pr.ready(epoch, lane, skip)) break;
         }
     }
     fence_acq_rel_gpu();
@@ -428,6 +431,69 @@ __device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT> &s,
     }
 }
 
+// Rows of a tile whose chunk records, indices and values sit in a
+// shared-memory stage (resident schedule): kRC chunks of a warp per pass, the
+// gathers of all their entries (kGb per row per pass) in flight together,
+// entries summed in stored order with padding skipped (as chunk_rows does, so
+// both round alike).  out(row, acc) writes a row.
+constexpr int kRC = 2;
+
+template <typename VT, typename MT, int G, typename Out>
+__device__ __forceinline__ void resident_rows(const ExecArgs &a, const int4 *srec, const int32_t *scol,
+                                              const MT *sval, int64_t ebase, int32_t nch, int warp, int ncw, int lane,
+                                              const VT *yin, const Out &out) {
+    for (int32_t cb = warp; cb < nch; cb += kRC * ncw) {
+        int32_t row[kRC], w[kRC], e0[kRC];
+        int32_t wmax = 0;
+#pragma unroll
+        for (int i = 0; i < kRC; i++) {
+            const int32_t c = cb + i * ncw;
+            row[i] = -1;
+            w[i] = 0;
+            e0[i] = 0;
+            if (c < nch) {
+                const int4 r = srec[c];
+                if (lane < r.y) {
+                    row[i] = a.row_map ? __ldg(a.row_map + r.x + lane) : r.x + lane;
+                    w[i] = r.w;
+                    e0[i] = (int32_t)((int64_t)r.z * kChunk - ebase) + lane;
+                }
+            }
+            wmax = max(wmax, w[i]);
+        }
+        VT acc[kRC][G];
+#pragma unroll
+        for (int i = 0; i < kRC; i++)
+#pragma unroll
+            for (int q = 0; q < G; q++) acc[i][q] = VT(0);
+        for (int32_t j0 = 0; j0 < wmax; j0 += kGb) {
+            int32_t cols[kRC][kGb];
+            VT g[kRC][kGb][G];
+#pragma unroll
+            for (int i = 0; i < kRC; i++)
+#pragma unroll
+                for (int u = 0; u < kGb; u++) {
+                    cols[i][u] = j0 + u < w[i] ? scol[e0[i] + (j0 + u) * kChunk] : -1;
+#pragma unroll
+                    for (int q = 0; q < G; q++)
+                        g[i][u][q] = cols[i][u] >= 0 ? yin[(int64_t)cols[i][u] * G + q] : VT(0);
+                }
+#pragma unroll
+            for (int i = 0; i < kRC; i++)
+#pragma unroll
+                for (int u = 0; u < kGb; u++)
+                    if (cols[i][u] >= 0) {
+                        const VT v = to_vt<MT, VT>(sval[e0[i] + (j0 + u) * kChunk]);
+#pragma unroll
+                        for (int q = 0; q < G; q++) acc[i][q] = fma(v, g[i][u][q], acc[i][q]);
+                    }
+        }
+#pragma unroll
+        for (int i = 0; i < kRC; i++)
+            if (row[i] >= 0) out(row[i], acc[i]);
+    }
+}
+
 // Body of one work item (tile t, power k) of the plain MPK.
 template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
 struct MpkNode {
@@ -451,6 +517,24 @@ struct MpkNode {
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
         for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps)
             chunk_rows<VT, MT, 1, true, DIAG, false>(a, mv, c, lane, yin, yout);
+    }
+
+    // resident schedule (block vectors of width W = nrhs in {1, 2})
+    template <typename Extra>
+    __device__ __forceinline__ static void res_run(const ExecArgs &a, const int4 *srec, const int32_t *scol,
+                                                   const MT *sval, int64_t ebase, int32_t nch, int32_t k, int warp,
+                                                   int nwarps, int lane, const Extra &) {
+        const VT *yin = k == 1 ? (const VT *)a.x : (const VT *)a.Y + (int64_t)(k - 2) * a.blk;
+        VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
+        resident_rows<VT, MT, W>(a, srec, scol, sval, ebase, nch, warp, nwarps, lane, yin,
+                                 [&](int32_t r, const VT (&acc)[W]) {
+#pragma unroll
+                                     for (int q = 0; q < W; q++) {
+                                         VT v = acc[q];
+                                         if (DIAG) v = fma((VT)__ldg(a.diag + r), yin[(int64_t)r * W + q], v);
+                                         yout[(int64_t)r * W + q] = v;
+                                     }
+                                 });
     }
 
     template <bool STAGED>
@@ -705,6 +789,182 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
     }
 }
 
+// ---------------------------------------------------------------- resident schedule
+// CTA b owns tiles b, b + G, b + 2G, ... (G = gridDim.x) and runs powers
+// 1..P of a tile before its next tile.  The tile's packed slice (chunk
+// records, column indices, values) is bulk-copied into a shared-memory stage
+// at its first power and read from there for all P powers: the matrix leaves
+// HBM once per sweep, the level-group blocking of Sec. 4 with shared memory
+// as the cache.  Two stages alternate, so the copy of a CTA's next tile runs
+// while it works on the current one.  The warp split, the flag protocol
+// (epoch-tagged completion flags, acquire before and release after an item,
+// publish before blocking) and the bounded waits are those of wave_loop.
+//
+// Cycle freedom: item (t, k) waits for items of power k-1 in tiles up to
+// t + span (span = max dep_hi[t] - t) and for item (t, k-1); the first power
+// of tile t waits for the CTA's previous tile t - G.  Along a chain of waits
+// the power falls at every dependency step, so a chain advances at most
+// (p-1)*span tiles before it has to step back G tiles: with G > (p-1)*span
+// (checked when the plan is built) no chain closes.
+template <typename MT>
+__device__ __forceinline__ void stage_tile(const ExecArgs &a, int32_t t, unsigned char *stage, uint64_t *mbar,
+                                           int32_t *s_nch, int64_t *s_ebase) {
+    const int32_t c0 = __ldg(a.tile_chunk + t), c1 = __ldg(a.tile_chunk + t + 1);
+    const int64_t o0 = __ldg(a.tile_off + t), o1 = __ldg(a.tile_off + t + 1);
+    const uint32_t rb = (uint32_t)(c1 - c0) * 16u, cb = (uint32_t)(o1 - o0) * 4u,
+                   vb = (uint32_t)(o1 - o0) * (uint32_t)sizeof(MT);
+    *s_nch = c1 - c0;
+    *s_ebase = o0;
+    const uint64_t pol = l2_policy_evict_first();   // read once per sweep
+    fence_proxy_async_smem();
+    mbar_expect_tx(mbar, rb + cb + vb);
+    unsigned char *cols = stage + (size_t)a.stage_recs * 16;
+    if (rb) bulk_g2s(stage, a.chunk_rec + c0, rb, mbar, pol);
+    if (cb) bulk_g2s(cols, a.pcol + o0, cb, mbar, pol);
+    if (vb) bulk_g2s(cols + (size_t)a.stage_entries * 4, (const MT *)a.pval + o0, vb, mbar, pol);
+}
+
+template <typename Node, typename MT, typename Extra>
+__device__ __forceinline__ void resident_loop(const ExecArgs &a, uint32_t epoch, const Extra &extra) {
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    __shared__ int s_item, s_stage;
+    __shared__ int32_t s_nch[2];
+    __shared__ int64_t s_ebase[2];
+    __shared__ __align__(8) uint64_t mbar[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncw = (int)(blockDim.x >> 5) - 1;
+    const int nthr = (int)blockDim.x;
+    const size_t rec_bytes = (size_t)a.stage_recs * 16;
+    const size_t stage_bytes = ((rec_bytes + (size_t)a.stage_entries * (4 + sizeof(MT)) + 127) / 128) * 128;
+    const int32_t P = a.p;
+    const int32_t G = (int32_t)gridDim.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == ncw) {
+        // ------------------------------------------------------------ scheduler warp
+        int32_t issued[2] = {0, 0}, consumed[2] = {0, 0};
+        auto issue = [&](int32_t q) {   // tile q of this CTA into stage q & 1
+            const int64_t t = (int64_t)blockIdx.x + (int64_t)q * G;
+            if (t < a.n_tiles) {
+                if (lane == 0)
+                    stage_tile<MT>(a, (int32_t)t, dsmem + (q & 1) * stage_bytes, &mbar[q & 1], &s_nch[q & 1],
+                                   &s_ebase[q & 1]);
+                issued[q & 1]++;
+            }
+        };
+        issue(0);
+        issue(1);
+        FlagProbe pr;
+        int32_t q = 0, k = 1, t = blockIdx.x;
+        bool ok = t < a.n_tiles;
+        if (lane == 0) {
+            s_item = ok ? ((t << 8) | 1) : -1;
+            s_stage = 0;
+        }
+        __syncwarp();
+        named_arrive(kBarReady, nthr);
+        while (ok) {
+            int32_t qn = q, kn = k + 1;
+            if (kn > P) {
+                qn = q + 1;
+                kn = 1;
+            }
+            const int64_t tn64 = (int64_t)blockIdx.x + (int64_t)qn * G;
+            const bool more = tn64 < a.n_tiles;
+            const int32_t tn = more ? (int32_t)tn64 : 0;
+            const int32_t self = qn == q ? t : -1;   // (t, k) is this CTA's own, finished before (t, k+1)
+            bool ready = true;
+            if (more && kn > 1) {
+                pr.issue(a, tn, kn, lane);
+                ready = pr.fits() ? pr.ready(epoch, lane, self) : ready_wide(a, tn, kn, epoch, lane, self);
+                if (ready) fence_acq_rel_gpu();
+            }
+            named_sync(kBarDone, nthr);   // compute warps finished (t, k)
+            if (k == P) consumed[q & 1]++;
+            auto publish = [&]() {
+                if (lane == 0 && !(t == a.drop_tile && k == a.drop_k))
+                    st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
+            };
+            if (!more) {
+                publish();
+                if (lane == 0) s_item = -1;
+                __syncwarp();
+                named_arrive(kBarReady, nthr);
+                break;
+            }
+            if (!ready) {   // publish first, then block on the next item's dependencies
+                publish();
+                ready = wait_deps(a, pr, tn, kn, epoch, lane, self);
+            }
+            if (ready && k == P) issue(q + 2);   // the stage of tile q is free
+            if (lane == 0) {
+                s_item = ready ? ((tn << 8) | kn) : -1;
+                s_stage = qn & 1;
+            }
+            __syncwarp();
+            named_arrive(kBarReady, nthr);
+            if (!ready) break;
+            publish();   // off the compute warps' critical path (a repeat store is harmless)
+            q = qn;
+            k = kn;
+            t = tn;
+        }
+        // never leave with a bulk copy in flight (abort path)
+        for (int st = 0; st < 2; st++)
+            while (consumed[st] < issued[st]) {
+                if (!mbar_wait(&mbar[st], (uint32_t)(consumed[st] & 1), a.timeout_ns) && lane == 0)
+                    record_timeout(a, 0, -1);
+                consumed[st]++;
+            }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            const int done = atomicAdd(a.ctl + CTL_FINISHED, 1);
+            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch, reset
+                atomicExch(a.ctl + CTL_FINISHED, 0);
+                atomicExch(a.ctl + CTL_ABORT, 0);
+                atomicExch(a.ctl + CTL_EPOCH, (int)epoch);
+                __threadfence();
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ compute warps
+        uint32_t ph[2] = {0u, 0u};
+        for (;;) {
+            named_sync(kBarReady, nthr);
+            const int32_t wk = *(volatile int *)&s_item;
+            const int st = *(volatile int *)&s_stage;
+            if (wk < 0) break;
+            const int32_t t = wk >> 8, k = wk & 255;
+            if (k == 1) {   // first power of the tile: its slice must have landed
+                const bool landed = mbar_wait(&mbar[st], ph[st], a.timeout_ns);
+                ph[st] ^= 1u;
+                if (!landed) {
+                    if (lane == 0) record_timeout(a, k, t);
+                    named_arrive(kBarDone, nthr);
+                    continue;
+                }
+            }
+            const unsigned char *sb = dsmem + st * stage_bytes;
+            Node::res_run(a, (const int4 *)sb, (const int32_t *)(sb + rec_bytes),
+                          (const MT *)(sb + rec_bytes + (size_t)a.stage_entries * 4), s_ebase[st], s_nch[st], k,
+                          warp, ncw, lane, extra);
+            named_arrive(kBarDone, nthr);
+        }
+    }
+}
+
+template <typename VT, typename MT, int W, bool DIAG>
+__global__ void __launch_bounds__(kResThreads) k_res_wave(ExecArgs a) {
+    const uint32_t epoch = (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u;
+    resident_loop<MpkNode<VT, MT, W, true, DIAG>, MT>(a, epoch, 0);
+}
+
 #if MPK_WAVE_MIN_BLOCKS > 0
 #define MPK_WAVE_BOUNDS __launch_bounds__(kWaveThreads, MPK_WAVE_MIN_BLOCKS)
 #else
@@ -816,6 +1076,14 @@ struct ChebNode {
         for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps) chunk<STAGED>(a, mv, c, lane, ca, v);
     }
 
+    __device__ __forceinline__ static void res_run(const ExecArgs &a, const int4 *srec, const int32_t *scol,
+                                                   const MT *sval, int64_t ebase, int32_t nch, int32_t j, int warp,
+                                                   int nwarps, int lane, const ChebArgs &ca) {
+        const Vecs v = vecs(a, ca, j);
+        resident_rows<VT, MT, 2>(a, srec, scol, sval, ebase, nch, warp, nwarps, lane, v.yin,
+                                 [&](int32_t r, const VT (&acc)[2]) { row_out(a, ca, v, r, acc[0], acc[1]); });
+    }
+
     __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT> &s, int32_t t, int32_t j,
                                                     int warp, int nwarps, int lane, const ChebArgs &ca) {
         const Vecs v = vecs(a, ca, j);
@@ -833,6 +1101,12 @@ template <typename VT, typename MT, bool DIAG, bool STAGED>
 __global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
     const OnePlan src{ca.e, (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u};
     wave_loop<ChebNode<VT, MT, DIAG>, MT, STAGED>(ca.e, src, ca);
+}
+
+template <typename VT, typename MT, bool DIAG>
+__global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
+    const uint32_t epoch = (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u;
+    resident_loop<ChebNode<VT, MT, DIAG>, MT>(ca.e, epoch, ca);
 }
 
 // ---------------------------------------------------------------- batched MPK
@@ -965,7 +1239,23 @@ const void *pick_cheb_t(const Plan *pl) {
     if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED>;
     return (const void *)k_cheb_wave<float, float, true, STAGED>;
 }
-const void *pick_wave(const Plan *pl) { return pl->staged ? pick_wave_t<true>(pl) : pick_wave_t<false>(pl); }
+template <int W>
+const void *pick_res_w(const Plan *pl) {
+    if (pl->prec == MPK_F64) return (const void *)k_res_wave<double, double, W, false>;
+    if (!pl->has_diag) return (const void *)k_res_wave<float, float, W, false>;
+    if (pl->val_bytes == 2) return (const void *)k_res_wave<float, __nv_bfloat16, W, true>;
+    return (const void *)k_res_wave<float, float, W, true>;
+}
+const void *pick_res_cheb(const Plan *pl) {
+    if (pl->prec == MPK_F64) return (const void *)k_res_cheb<double, double, false>;
+    if (!pl->has_diag) return (const void *)k_res_cheb<float, float, false>;
+    if (pl->val_bytes == 2) return (const void *)k_res_cheb<float, __nv_bfloat16, true>;
+    return (const void *)k_res_cheb<float, float, true>;
+}
+const void *pick_wave(const Plan *pl) {
+    if (pl->resident) return pl->nrhs == 1 ? pick_res_w<1>(pl) : pick_res_w<2>(pl);
+    return pl->staged ? pick_wave_t<true>(pl) : pick_wave_t<false>(pl);
+}
 
 }  // namespace
 
@@ -975,7 +1265,10 @@ const void *batch_kernel(int prec) {
 
 namespace {
 
-const void *pick_cheb(const Plan *pl) { return pl->staged ? pick_cheb_t<true>(pl) : pick_cheb_t<false>(pl); }
+const void *pick_cheb(const Plan *pl) {
+    if (pl->resident) return pick_res_cheb(pl);
+    return pl->staged ? pick_cheb_t<true>(pl) : pick_cheb_t<false>(pl);
+}
 const void *pick_spmv(const Plan *pl) {
     if (pl->prec == MPK_F64) return spmv_ptr<double, double, false>(pl->nrhs);
     if (!pl->has_diag) return spmv_ptr<float, float, false>(pl->nrhs);
@@ -995,7 +1288,7 @@ int wave_occupancy(const Plan *pl, int *ctas_per_sm) {
         if (!fn) continue;
         MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes));
         int o = 0;
-        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kWaveThreads, pl->smem_bytes));
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, wave_threads(pl), pl->smem_bytes));
         occ = std::min(occ, o);
     }
     *ctas_per_sm = occ;
@@ -1030,6 +1323,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.tile_off = pl->d_tile_off;
     a.row_map = pl->d_row_map;
     a.chunk_rec = pl->d_chunk_rec;
+    a.stage_recs = pl->stage_recs;
     a.stage_entries = pl->stage_entries;
     a.tune = pl->tune;
     return a;
@@ -1037,10 +1331,10 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
 
 // Cooperative launch (all CTAs co-resident), expressed with cudaLaunchKernelEx
 // so that it can also be captured in a CUDA graph.
-int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st) {
+int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st, int threads) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kWaveThreads);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1071,7 +1365,7 @@ int launch_wavefront(Plan *pl, const void *x, void *Y, cudaStream_t st) {
     a.drop_k = pl->drop_k;
     pl->drop_tile = pl->drop_k = -1;
     void *args[] = {(void *)&a};
-    return launch_coop(pick_wave(pl), pl->grid_ctas, pl->smem_bytes, args, st);
+    return launch_coop(pick_wave(pl), pl->grid_ctas, pl->smem_bytes, args, st, wave_threads(pl));
 }
 
 int launch_baseline(Plan *pl, const void *x, void *Y, cudaStream_t st) {
@@ -1291,7 +1585,7 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
         }
         ca.k0 = k0;
         void *args[] = {(void *)&ca};
-        if ((rc = launch_coop(pick_cheb(pl), pl->grid_ctas, pl->smem_bytes, args, st))) return rc;
+        if ((rc = launch_coop(pick_cheb(pl), pl->grid_ctas, pl->smem_bytes, args, st, wave_threads(pl)))) return rc;
     }
     if (!(flags & MPK_IO_PERMUTED)) {
         // acc (level order, n x 2 doubles) -> y (original order)

@@ -22,6 +22,11 @@ constexpr int kMaxNrhs = 64;
 constexpr int kComputeWarps = MPK_COMPUTE_WARPS;         // warps that compute work items
 constexpr int kWaveThreads = (kComputeWarps + 1) * 32;   // plus one scheduler warp
 constexpr int kSpmvThreads = 256;                        // baseline SpMV CTA
+#ifndef MPK_RES_WARPS
+#define MPK_RES_WARPS 16
+#endif
+constexpr int kResWarps = MPK_RES_WARPS;                 // compute warps of a resident-schedule CTA
+constexpr int kResThreads = (kResWarps + 1) * 32;
 
 // Control words of a plan (device int32 array).
 enum Ctl : int {
@@ -56,6 +61,10 @@ struct Plan {
     uint32_t tune = 0;              // MPK_TUNE_* bits
     int32_t staged = 0;             // matrix slices staged in shared memory by bulk copies
     int32_t sorted = 0;             // rows of each tile packed in order of decreasing length
+    int32_t resident = 0;           // resident schedule (a CTA keeps a tile's slice for all powers)
+    int32_t dep_span = 0;           // max over tiles of dep_hi[t] - t
+    int32_t stage_recs = 0;         // chunk records one resident stage holds
+    int32_t max_row_len = 0;        // longest row of P A P^T
     int32_t *d_row_map = nullptr;   // packed position -> row (only when sorted)
     int64_t stage_entries = 0;      // capacity of one stage in packed entries
     size_t smem_bytes = 0;          // dynamic shared memory per wavefront CTA
@@ -113,6 +122,7 @@ struct ExecArgs {
     uint32_t tune;               // MPK_TUNE_* bits
     const int32_t *row_map;      // chunk position -> row (rows sorted by length in a tile); null = identity
     const int4 *chunk_rec;       // per chunk {first row, rows, first entry / 32, width}
+    int32_t stage_recs;          // chunk records one resident stage holds
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).
@@ -174,9 +184,10 @@ int ensure_io(Plan *pl, size_t bytes);
 double order_items(const Plan *pl, int32_t p_sweep, double lag, std::vector<int32_t> &work);
 int wave_occupancy(const Plan *pl, int *ctas_per_sm);
 const void *batch_kernel(int prec);
-int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st);
+int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st, int threads = kWaveThreads);
 
 inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
+inline int wave_threads(const Plan *pl) { return pl->resident ? kResThreads : kWaveThreads; }
 
 }  // namespace mpk
 

@@ -717,6 +717,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         f[1] = (float)mean;
         f[2] = (float)std::sqrt(var);
         f[3] = (float)std::log10(1.0 + (double)h[2]);
+        pl->max_row_len = (int32_t)h[2];
         f[4] = (float)((double)h[3] / std::max(1.0, (double)h[0]) / N);   // mean |col-row| / N
         f[5] = (float)((double)h[4] / N);                                  // max |col-row| / N
     }
@@ -790,7 +791,25 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     // (CTAs x tile rows) stay a small part of the level-group window, large
     // enough to amortise the per-item synchronisation; tiny matrices get
     // smaller tiles so that every SM has work.
+    //    Resident schedule: a tile must fit one of the two shared-memory
+    //    stages of its CTA; rows are at most max_row_len entries wide, so
+    //    tile_rows * max_row_len entries (plus a record per chunk) bound it.
+    const bool want_res = (o->tune & MPK_TUNE_RESIDENT) && (o->nrhs == 1 || o->nrhs == 2);
+    const int res_per_sm = std::max(1, std::min(2, o->ctas_per_sm > 0 ? o->ctas_per_sm : 1));
+    size_t res_stage = 0;
+    if (want_res) {
+        const size_t per_cta = std::min<size_t>((size_t)prop.sharedMemPerBlockOptin,
+                                                (size_t)prop.sharedMemPerMultiprocessor / res_per_sm) -
+                               2048;   // static shared memory and the per-CTA reservation
+        res_stage = (per_cta / 2) / 128 * 128;
+    }
     int32_t tr = o->tile_rows;
+    if (tr <= 0 && want_res) {
+        const double per_row = (double)std::max(1, pl->max_row_len) * (double)(4 + pl->val_bytes) + 16.0 / kChunk;
+        const int64_t rows = (int64_t)((double)(res_stage - 256) / per_row);
+        tr = (int32_t)std::min<int64_t>(8192, (rows / kChunk) * kChunk);
+        if (tr < kChunk) tr = 0;   // rows too wide for a stage: work-list schedule
+    }
     if (tr <= 0) {
         int64_t target = (int64_t)n / ((int64_t)pl->num_sms * 4);
         tr = (int32_t)std::min<int64_t>(512, std::max<int64_t>(kChunk, (target / kChunk) * kChunk));
@@ -906,28 +925,60 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         MPK_CUDA(cudaMemcpyAsync(toff.data(), pl->d_tile_off, sizeof(int64_t) * toff.size(), cudaMemcpyDeviceToHost, st));
         MPK_CUDA(cudaStreamSynchronize(st));
         int64_t mx = 0;
-        for (int32_t t = 0; t < pl->n_tiles; t++) mx = std::max(mx, toff[t + 1] - toff[t]);
+        int32_t mc = 0;
+        for (int32_t t = 0; t < pl->n_tiles; t++) {
+            mx = std::max(mx, toff[t + 1] - toff[t]);
+            mc = std::max(mc, tile_chunk[t + 1] - tile_chunk[t]);
+        }
         pl->stage_entries = ((mx + kChunk - 1) / kChunk) * kChunk;
-        const size_t need = 2 * (size_t)pl->stage_entries * (size_t)(4 + pl->val_bytes);
+        pl->stage_recs = ((mc + 7) / 8) * 8;
         pl->tune = o->tune;
-        pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
-        pl->smem_bytes = pl->staged ? need : 0;
+        const size_t res_need =
+            (((size_t)pl->stage_recs * 16 + (size_t)pl->stage_entries * (4 + pl->val_bytes) + 127) / 128) * 128;
+        if (want_res && res_need <= res_stage) {
+            pl->resident = 1;
+            pl->staged = 0;
+            pl->smem_bytes = 2 * res_need;
+        } else {
+            const size_t need = 2 * (size_t)pl->stage_entries * (size_t)(4 + pl->val_bytes);
+            pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
+            pl->smem_bytes = pl->staged ? need : 0;
+        }
     }
 
     // 11. grid size, then the work list: a skewed diagonal order of the Lp
     //     diagram over level groups (see order_items)
-    int occ = 0;
-    MPK_TRY(wave_occupancy(pl, &occ));
-    int per_sm = o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : occ;
-    pl->ctas_per_sm = std::max(1, per_sm);
-    {
+    pl->h_dep_hi.resize((size_t)pl->n_tiles);
+    MPK_CUDA(cudaMemcpyAsync(pl->h_dep_hi.data(), pl->d_dep_hi, sizeof(int32_t) * pl->h_dep_hi.size(),
+                             cudaMemcpyDeviceToHost, st));
+    MPK_CUDA(cudaStreamSynchronize(st));
+    for (int32_t t = 0; t < pl->n_tiles; t++) pl->dep_span = std::max(pl->dep_span, pl->h_dep_hi[t] - t);
+    if (pl->resident) {
+        // resident schedule: res_per_sm CTAs per SM, each owning whole tiles;
+        // the wait chains cannot close when G > (p-1) * span (or every tile
+        // has its own CTA)
+        int occ = 0;
+        MPK_TRY(wave_occupancy(pl, &occ));
+        const int64_t G = std::min<int64_t>((int64_t)pl->num_sms * res_per_sm, pl->n_tiles);
+        const bool acyclic = G >= pl->n_tiles || G > (int64_t)(p - 1) * pl->dep_span;
+        if (occ >= res_per_sm && acyclic) {
+            pl->ctas_per_sm = res_per_sm;
+            pl->grid_ctas = (int32_t)G;
+        } else {
+            pl->resident = 0;
+            pl->smem_bytes = 0;
+        }
+    }
+    if (!pl->resident) {
+        int occ = 0;
+        MPK_TRY(wave_occupancy(pl, &occ));
+        int per_sm = o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : occ;
+        pl->ctas_per_sm = std::max(1, per_sm);
         const int64_t items = (int64_t)pl->n_tiles * p;
         pl->grid_ctas =
             (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)pl->num_sms * pl->ctas_per_sm, items));
-        pl->h_dep_hi.resize((size_t)pl->n_tiles);
-        MPK_CUDA(cudaMemcpyAsync(pl->h_dep_hi.data(), pl->d_dep_hi, sizeof(int32_t) * pl->h_dep_hi.size(),
-                                 cudaMemcpyDeviceToHost, st));
-        MPK_CUDA(cudaStreamSynchronize(st));
+    }
+    {
         pl->h_tile_row = tile_row;
         pl->h_group_tile = group_tile;
         std::vector<int32_t> work;
@@ -1116,6 +1167,8 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->slope = pl.slope;
     s->staged = pl.staged;
     s->sorted = pl.sorted;
+    s->resident = pl.resident;
+    s->dep_span = pl.dep_span;
     s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
 }
