@@ -41,13 +41,13 @@ def test_resident_f64_matches_oracle(name, p):
 def test_resident_many_tiles_per_cta(tile_rows, ctas, prec):
     """Small explicit tiles: each CTA runs many tiles in turn, both stages
     alternate, and the grid is far below the tile count."""
-    A = mi.laplace2d(200, 150)
+    A = mi.laplace2d(300, 200)
     p = 8
     x = mi.random_vector(A.n, 5)
     ref = oracle.mpk(A, x, p)
     plan = plan_of(A, p, prec=prec, tile_rows=tile_rows, ctas_per_sm=ctas, tune=RES)
     info = mpk.mpk_plan_info(plan)
-    assert info["resident"] == 1 and info["n_tiles"] > 2 * info["grid_ctas"]
+    assert info["resident"] == 1 and info["n_tiles"] > 1.5 * info["grid_ctas"]
     assert info["grid_ctas"] > (p - 1) * info["dep_span"]
     xin = x if prec == "f64" else x.astype(np.float32)
     got = run_mpk(plan, xin)
