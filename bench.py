@@ -58,6 +58,35 @@ def make_matrix(kind, size):
     return getattr(mi, kind)(size)
 
 
+def kernel_sources_hash():
+    """sha256 prefix of the sources that define the MPK kernels and the plan's
+    data layout (mpk_exec.cu, mpk_plan.cu, mpk_internal.cuh, in that order):
+    a change to any of them invalidates a recorded ncu capture."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2205_01598_gb300", "csrc")
+    for name in ("mpk_exec.cu", "mpk_plan.cu", "mpk_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(summary, prec):
+    """DRAM bytes (read + write) per launch of the dominant kernel from the
+    committed ncu summary, or None once the kernel sources have changed since
+    the capture (or no capture covers this precision)."""
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        with open(path) as f:
+            line = next(l for l in f if l.startswith("traffic-bytes-per-launch:"))
+    except (OSError, StopIteration):
+        return None
+    fields = dict(kv.split("=", 1) for kv in line.split(":", 1)[1].split())
+    if fields.get("sources") != kernel_sources_hash() or prec not in fields:
+        return None
+    return int(fields[prec])
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -255,18 +284,19 @@ def main():
     value_e2e = ws * flops / (ms_e2e * 1e-3) / 1e9
 
     peaks, peak_src = load_peaks()
+    traffic = recorded_traffic("k_wave_laplace3d160_p8.md", prec) if (kind, size, p) == ("laplace3d", 160, 8) else None
     # the FP64 path is bound by FP64 arithmetic (1 FMA per stored entry and power)
     if prec == "f64":
         achieved = flops / (ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "peak_source": "nominal FP64 rate of the profiling recipe"}
     else:
         vb = 4
         alg_bytes = info["nnz"] * (vb + 4) + (A.n + 1) * 4 + A.n * vb * (1 + p)
         achieved = alg_bytes / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": peak_src}
 
     cpu = None

@@ -275,10 +275,11 @@ typedef struct {
 } mpk_tune_candidate;
 
 /* Fills out[0..*count) with the default search grid for k powers: entry 0 is
- * the library's default options (tile_rows 0, f 0.5, p_sweep k), then work
- * items of 64/128/256/512/1024 rows x f in {0.25, 0.5} x p_sweep in {k,
- * ceil(k/2) when k >= 4, 1 when k >= 2}.  MPK_ERR_INVALID if max is too small
- * (count = entries written).                                                 */
+ * the library's default options (tile_rows 0, f 0.5, p_sweep k); then the
+ * resident schedule (MPK_TUNE_RESIDENT, tiles sized to the stage) for p_sweep
+ * in {k, ceil(k/2) when k >= 4}; then work items of 64/128/256/512/1024 rows
+ * x f in {0.25, 0.5} x p_sweep in {k, ceil(k/2) when k >= 4, 1 when k >= 2}.
+ * MPK_ERR_INVALID if max is too small (count = entries written).            */
 int mpk_tune_default_grid(int32_t k, mpk_tune_candidate *out, int32_t max, int32_t *count);
 
 /* Times every candidate for the MPK of A with k powers (opts from *base with

@@ -58,11 +58,11 @@ extern "C" {
 int mpk_tune_default_grid(int32_t k, mpk_tune_candidate *out, int32_t max, int32_t *count) {
     if (!out || !count || k < 1) return MPK_ERR_INVALID;
     std::vector<mpk_tune_candidate> g;
-    auto add = [&](int32_t t, double f, int32_t q) {
+    auto add = [&](int32_t t, double f, int32_t q, uint32_t tune = 0) {
         mpk_tune_candidate r{};
         r.tile_rows = t;
         r.safety_f = f;
-        r.tune = 0;
+        r.tune = tune;
         r.p_sweep = q;
         r.ms = -1;
         r.status = 0;
@@ -71,6 +71,7 @@ int mpk_tune_default_grid(int32_t k, mpk_tune_candidate *out, int32_t max, int32
     add(0, 0.5, k);   // the library's default options
     std::vector<int32_t> sweeps = {k};
     if (k >= 4) sweeps.push_back((k + 1) / 2);
+    for (int32_t q : sweeps) add(0, 0.5, q, MPK_TUNE_RESIDENT);   // tiles sized to the stage
     if (k >= 2) sweeps.push_back(1);
     const int32_t tiles[] = {64, 128, 256, 512, 1024};
     const double fs[] = {0.25, 0.5};

@@ -61,9 +61,10 @@ def test_default_grid_layout(lib):
     from paper_2205_01598_gb300 import mpk_tune_default_grid
     g = mpk_tune_default_grid(8)
     assert g[0] == {"tile_rows": 0, "safety_f": 0.5, "tune": 0, "p_sweep": 8}
-    assert len(g) == 1 + 5 * 2 * 3
+    assert [c["tune"] for c in g[1:3]] == [8, 8] and [c["p_sweep"] for c in g[1:3]] == [8, 4]
+    assert len(g) == 1 + 2 + 5 * 2 * 3
     assert {c["p_sweep"] for c in g} == {8, 4, 1}
-    assert len(mpk_tune_default_grid(1)) == 1 + 5 * 2
+    assert len(mpk_tune_default_grid(1)) == 1 + 1 + 5 * 2
 
 
 def test_autotune_table(lib):
