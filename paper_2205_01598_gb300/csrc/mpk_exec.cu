@@ -175,11 +175,8 @@ struct FlagProbe {
     int32_t lo, hi, base;
 
     __device__ __forceinline__ void issue(const ExecArgs &a, int32_t t, int32_t k, int lane) {
-        issue_range(a, __ldg(a.dep_lo + t), __ldg(a.dep_hi + t), k, lane);
-    }
-    __device__ __forceinline__ void issue_range(const ExecArgs &a, int32_t dlo, int32_t dhi, int32_t k, int lane) {
-        lo = dlo;
-        hi = dhi;
+        lo = __ldg(a.dep_lo + t);
+        hi = __ldg(a.dep_hi + t);
         base = lo & ~3;
         const uint32_t *f = a.flags + (int64_t)(k - 1) * a.fstride;
 #pragma unroll
@@ -332,43 +329,30 @@ __device__ __forceinline__ void warp_chunks_staged(const ExecArgs &a, const MatV
     }
 }
 
-// ---------------------------------------------------------------- staged slices of the work-list schedule
+// ---------------------------------------------------------------- register-held slices
 // A compute warp handles chunks c0 + warp + i*ncw of a work item's tile.  The
-// first kPC of them (their first kPE entry rows: indices and values) are
-// copied into a double buffer of the warp in shared memory with 16-byte
-// asynchronous copies one work item ahead: those copies read only the
-// matrix, never a vector, so they are issued when the previous item starts,
-// before the item's own dependencies are known to be complete.  Once the
-// item is released, only the gathers of the input vector remain on its
-// critical path.  Chunk records and the items' chunk ranges are loaded two
-// and three items ahead into registers.
+// first kPC of them -- chunk record, row, and the first kPE entries of the
+// lane's row -- are loaded into registers one work item ahead.  Those loads
+// read only the matrix, never a vector, so they are issued before the item's
+// dependencies are known to be complete; once the item is released only the
+// gathers of the input vector remain on its critical path.
 #ifndef MPK_PIPE_CHUNKS
 #define MPK_PIPE_CHUNKS 2
 #endif
 #ifndef MPK_PIPE_ENTRIES
 #define MPK_PIPE_ENTRIES 8
 #endif
-constexpr int kPC = MPK_PIPE_CHUNKS;    // chunks of a warp staged per item
-constexpr int kPE = MPK_PIPE_ENTRIES;   // entry rows of a chunk staged
-
-// Shared-memory bytes of one staged slice (one buffer of one warp).
-__host__ __device__ constexpr size_t slice_bytes(int val_bytes) {
-    return (size_t)kPC * kPE * kChunk * (4 + (size_t)val_bytes);
-}
+constexpr int kPC = MPK_PIPE_CHUNKS;    // chunks of a warp held in registers
+constexpr int kPE = MPK_PIPE_ENTRIES;   // entries of a row held in registers
 
 template <typename MT>
 struct Slice {
-    int4 rec[kPC];      // {first row, rows, first entry / 32, width}; rows 0 = no chunk
-    const int32_t *col;  // [kPC][kPE][32] in shared memory
-    const MT *val;       // [kPC][kPE][32] in shared memory
-    int32_t c0, c1;     // chunk range of the item's tile
+    int4 rec[kPC];           // {first row, rows, first entry / 32, width}; rows 0 = no chunk
+    int32_t row[kPC];        // output row of this lane, -1 = none
+    int32_t col[kPC][kPE];   // -1 = past the row's end
+    MT val[kPC][kPE];
+    int32_t c0, c1;          // chunk range of the item's tile
 };
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void slice_recs(const ExecArgs &a, int32_t c0, int32_t c1, int warp, int ncw,
                                            int4 (&rec)[kPC]) {
@@ -379,46 +363,36 @@ __device__ __forceinline__ void slice_recs(const ExecArgs &a, int32_t c0, int32_
     }
 }
 
-// Copies of the first min(width, kPE) entry rows of the held chunks into a
-// buffer (same column-major layout as the packed arrays: entry row u of a
-// chunk is 32 consecutive indices / values).  Packed chunks start at
-// multiples of 32 entries, so every 16-byte piece is aligned.
 template <typename MT>
-__device__ __forceinline__ void stage_slice(const ExecArgs &a, const int4 (&rec)[kPC], int32_t *col, MT *val,
-                                            int lane) {
-    constexpr int per = 16 / (int)sizeof(MT);   // values per 16-byte piece
+__device__ __forceinline__ void slice_entries(const ExecArgs &a, Slice<MT> &s, int lane) {
 #pragma unroll
     for (int i = 0; i < kPC; i++) {
-        const int32_t w = rec[i].y > 0 ? min(rec[i].w, kPE) : 0;
-        const int64_t e0 = (int64_t)rec[i].z * kChunk;
-        for (int q = lane; q < w * (kChunk / 4); q += 32) cp_async16(col + i * kPE * kChunk + q * 4, a.pcol + e0 + q * 4);
-        for (int q = lane; q < w * (kChunk / per); q += 32)
-            cp_async16(val + i * kPE * kChunk + q * per, (const MT *)a.pval + e0 + q * per);
+        const int4 r = s.rec[i];
+        const bool on = lane < r.y;
+        s.row[i] = on ? (a.row_map ? __ldg(a.row_map + r.x + lane) : r.x + lane) : -1;
+        const int64_t e0 = (int64_t)r.z * kChunk + lane;
+#pragma unroll
+        for (int u = 0; u < kPE; u++) {
+            const bool in = on && u < r.w;
+            s.col[i][u] = in ? __ldg(a.pcol + e0 + (int64_t)u * kChunk) : -1;
+            s.val[i][u] = in ? __ldg((const MT *)a.pval + e0 + (int64_t)u * kChunk) : MT{};
+        }
     }
-    cp_async_commit();
 }
 
 // acc[i][q] = sum over the entries of the lane's row in held chunk i of
 // value * yin[col * G + q], in entry order (the order of chunk_rows, so both
-// paths round alike); row[i] = the lane's output row, -1 for none.  All
-// gathers of the staged entries are issued first; entries past kPE come from
-// global memory.
+// paths round alike).  All gathers of the held entries are issued first.
 template <typename VT, typename MT, int G>
 __device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT> &s, const VT *yin, int lane,
-                                          int32_t (&row)[kPC], VT (&acc)[kPC][G]) {
-    int32_t cols[kPC][kPE];
+                                          VT (&acc)[kPC][G]) {
     VT g[kPC][kPE][G];
 #pragma unroll
-    for (int i = 0; i < kPC; i++) {
-        const bool on = lane < s.rec[i].y;
-        row[i] = on ? (a.row_map ? __ldg(a.row_map + s.rec[i].x + lane) : s.rec[i].x + lane) : -1;
+    for (int i = 0; i < kPC; i++)
 #pragma unroll
-        for (int u = 0; u < kPE; u++) {
-            cols[i][u] = on && u < s.rec[i].w ? s.col[(i * kPE + u) * kChunk + lane] : -1;
+        for (int u = 0; u < kPE; u++)
 #pragma unroll
-            for (int q = 0; q < G; q++) g[i][u][q] = cols[i][u] >= 0 ? yin[(int64_t)cols[i][u] * G + q] : VT(0);
-        }
-    }
+            for (int q = 0; q < G; q++) g[i][u][q] = s.col[i][u] >= 0 ? yin[(int64_t)s.col[i][u] * G + q] : VT(0);
 #pragma unroll
     for (int i = 0; i < kPC; i++)
 #pragma unroll
@@ -427,32 +401,32 @@ __device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT> &s,
     for (int i = 0; i < kPC; i++)
 #pragma unroll
         for (int u = 0; u < kPE; u++)
-            if (cols[i][u] >= 0) {
-                const VT v = to_vt<MT, VT>(s.val[(i * kPE + u) * kChunk + lane]);
+            if (s.col[i][u] >= 0) {
+                const VT v = to_vt<MT, VT>(s.val[i][u]);
 #pragma unroll
                 for (int q = 0; q < G; q++) acc[i][q] = fma(v, g[i][u][q], acc[i][q]);
             }
-    // entries past the staged ones (rows wider than kPE)
+    // entries past the held ones (rows wider than kPE)
 #pragma unroll
     for (int i = 0; i < kPC; i++) {
         const int32_t w = s.rec[i].w;
-        if (row[i] < 0 || w <= kPE) continue;
+        if (s.row[i] < 0 || w <= kPE) continue;
         const int64_t e0 = (int64_t)s.rec[i].z * kChunk + lane;
         constexpr int B = 8;
         for (int32_t j0 = kPE; j0 < w; j0 += B) {
-            int32_t cb[B];
+            int32_t cols[B];
             VT vals[B];
 #pragma unroll
             for (int u = 0; u < B; u++) {
                 const bool in = j0 + u < w;
-                cb[u] = in ? __ldg(a.pcol + e0 + (int64_t)(j0 + u) * kChunk) : -1;
+                cols[u] = in ? __ldg(a.pcol + e0 + (int64_t)(j0 + u) * kChunk) : -1;
                 vals[u] = in ? to_vt<MT, VT>(__ldg((const MT *)a.pval + e0 + (int64_t)(j0 + u) * kChunk)) : VT(0);
             }
 #pragma unroll
             for (int u = 0; u < B; u++)
-                if (cb[u] >= 0)
+                if (cols[u] >= 0)
 #pragma unroll
-                    for (int q = 0; q < G; q++) acc[i][q] = fma(vals[u], yin[(int64_t)cb[u] * G + q], acc[i][q]);
+                    for (int q = 0; q < G; q++) acc[i][q] = fma(vals[u], yin[(int64_t)cols[u] * G + q], acc[i][q]);
         }
     }
 }
@@ -531,11 +505,10 @@ struct MpkNode {
         const VT *yin = k == 1 ? (const VT *)a.x : (const VT *)a.Y + (int64_t)(k - 2) * a.blk;
         VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
         VT acc[kPC][1];
-        int32_t row[kPC];
-        slice_sum<VT, MT, 1>(a, s, yin, lane, row, acc);
+        slice_sum<VT, MT, 1>(a, s, yin, lane, acc);
 #pragma unroll
         for (int i = 0; i < kPC; i++) {
-            const int32_t r = row[i];
+            const int32_t r = s.row[i];
             if (r < 0) continue;
             VT v = acc[i][0];
             if (DIAG) v = fma((VT)__ldg(a.diag + r), yin[r], v);
@@ -647,80 +620,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
     }
     __syncthreads();
 
-    if (warp == ncw && !STAGED && std::is_same<Src, OnePlan>::value) {
-        // ------------------------------------------------------------ scheduler warp, one plan
-        // Item descriptors {item, dep_lo, dep_hi} are loaded two items ahead, and
-        // the flags of the next item are probed while the current one runs, so
-        // that its readiness is known when the compute warps finish.
-        const ExecArgs &a = src.args(0);
-        const uint32_t epoch = src.epoch_of(0);
-        const int64_t G = gridDim.x;
-        int64_t j = blockIdx.x;
-        auto desc = [&](int64_t jj) { return jj < g.n_items ? __ldg(g.item_desc + jj) : make_int4(-1, 0, -1, 0); };
-        int4 d0 = desc(j), d1 = desc(j + G), d2 = desc(j + 2 * G);
-        FlagProbe pr;
-        bool ok = d0.x >= 0;
-        if (ok && (d0.x & 255) > 1) {
-            pr.issue(a, d0.x >> 8, d0.x & 255, lane);
-            ok = wait_deps(a, pr, d0.x >> 8, d0.x & 255, epoch, lane);
-        }
-        if (lane == 0) {
-            s_item = ok ? d0.x : -1;
-            s_plan = 0;
-            s_stage = 0;
-        }
-        __syncwarp();
-        named_arrive(kBarReady, nthr);
-        while (ok) {
-            const int32_t wn = d1.x;
-            const bool more = wn >= 0;
-            const bool deps = more && (wn & 255) > 1;
-            if (deps) pr.issue_range(a, d1.y, d1.z, wn & 255, lane);
-            const int4 d3 = desc(j + 3 * G);
-            bool ready = true;
-            if (deps) {
-                ready = pr.fits() ? pr.ready(epoch, lane) : ready_wide(a, wn >> 8, wn & 255, epoch, lane);
-                if (ready) fence_acq_rel_gpu();
-            }
-            named_sync(kBarDone, nthr);   // compute warps finished item j
-            const int32_t t = d0.x >> 8, k = d0.x & 255;
-            auto publish = [&]() {
-                if (lane == 0 && !(t == a.drop_tile && k == a.drop_k))
-                    st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
-            };
-            if (!more) {
-                publish();
-                if (lane == 0) s_item = -1;
-                __syncwarp();
-                named_arrive(kBarReady, nthr);
-                break;
-            }
-            if (!ready) {   // publish first, then block on the next item's dependencies
-                publish();
-                ready = wait_deps(a, pr, wn >> 8, wn & 255, epoch, lane);
-            }
-            if (lane == 0) s_item = ready ? wn : -1;
-            __syncwarp();
-            named_arrive(kBarReady, nthr);
-            if (!ready) break;
-            publish();   // off the compute warps' critical path (a repeat store is harmless)
-            d0 = d1;
-            d1 = d2;
-            d2 = d3;
-            j += G;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            const int done = atomicAdd(g.ctl + CTL_FINISHED, 1);
-            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch, reset
-                atomicExch(g.ctl + CTL_FINISHED, 0);
-                atomicExch(g.ctl + CTL_ABORT, 0);
-                src.publish_epochs();
-                __threadfence();
-            }
-        }
-    } else if (warp == ncw) {
+    if (warp == ncw) {
         // ------------------------------------------------------------ scheduler warp
         const int G = (int)gridDim.x;
         int32_t issued[2] = {0, 0}, consumed[2] = {0, 0};   // bulk copies per stage
@@ -822,52 +722,43 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             }
         }
     } else if constexpr (!STAGED && Node::kPipe && std::is_same<Src, OnePlan>::value) {
-        // ------------------------------------------------------------ compute warps, staged slices
+        // ------------------------------------------------------------ compute warps, register-held slices
         const ExecArgs &a = src.args(0);
         const int64_t G = gridDim.x;
         int64_t j = blockIdx.x;
-        const size_t sb = slice_bytes((int)sizeof(MT));
-        unsigned char *wbuf = dsmem + (size_t)warp * 2 * sb;   // this warp's two buffers
-        auto bcol = [&](int b) { return (int32_t *)(wbuf + b * sb); };
-        auto bval = [&](int b) { return (MT *)(wbuf + b * sb + (size_t)kPC * kPE * kChunk * 4); };
-        auto range = [&](int64_t jj) { return jj < g.n_items ? __ldg(g.item_chunks + jj) : make_int2(0, 0); };
-        int2 rg = range(j), rgN = range(j + G), rgNN = range(j + 2 * G);
-        int4 rec[kPC], recN[kPC];
-        slice_recs(a, rg.x, rg.y, warp, ncw, rec);
-        stage_slice<MT>(a, rec, bcol(0), bval(0), lane);
-        slice_recs(a, rgN.x, rgN.y, warp, ncw, recN);
-        int b = 0;
+        auto range = [&](int64_t jj, int32_t &c0, int32_t &c1) {
+            c0 = c1 = 0;
+            if (jj < g.n_items) {
+                const int32_t t = __ldg(g.work + jj) >> 8;
+                c0 = __ldg(a.tile_chunk + t);
+                c1 = __ldg(a.tile_chunk + t + 1);
+            }
+        };
+        Slice<MT> s;
+        range(j, s.c0, s.c1);
+        slice_recs(a, s.c0, s.c1, warp, ncw, s.rec);
+        slice_entries(a, s, lane);
+        int32_t n0, n1;   // chunk range of item j + G
+        range(j + G, n0, n1);
         for (;;) {
             named_sync(kBarReady, nthr);
             const int32_t wk = *(volatile int *)&s_item;
             if (wk < 0) break;
-            cp_async_wait_all();   // slice of this item (copied during the previous one)
-            __syncwarp();
-            stage_slice<MT>(a, recN, bcol(b ^ 1), bval(b ^ 1), lane);   // item j + G
-            int4 recNN[kPC];
-            slice_recs(a, rgNN.x, rgNN.y, warp, ncw, recNN);             // item j + 2G
-            const int2 rgNNN = range(j + 3 * G);
-            Slice<MT> s;
-#pragma unroll
-            for (int i = 0; i < kPC; i++) s.rec[i] = rec[i];
-            s.col = bcol(b);
-            s.val = bval(b);
-            s.c0 = rg.x;
-            s.c1 = rg.y;
+            int4 rn[kPC];   // records of item j + G, and the chunk range of item j + 2G
+            slice_recs(a, n0, n1, warp, ncw, rn);
+            int32_t m0, m1;
+            range(j + 2 * G, m0, m1);
             Node::pipe_run(a, s, wk >> 8, wk & 255, warp, ncw, lane, extra);
+            s.c0 = n0;
+            s.c1 = n1;
 #pragma unroll
-            for (int i = 0; i < kPC; i++) {
-                rec[i] = recN[i];
-                recN[i] = recNN[i];
-            }
-            rg = rgN;
-            rgN = rgNN;
-            rgNN = rgNNN;
-            b ^= 1;
+            for (int i = 0; i < kPC; i++) s.rec[i] = rn[i];
+            slice_entries(a, s, lane);   // item j + G, used after its release
+            n0 = m0;
+            n1 = m1;
             j += G;
             named_arrive(kBarDone, nthr);
         }
-        cp_async_wait_all();   // never leave with a copy in flight
     } else {
         // ------------------------------------------------------------ compute warps
         uint32_t ph0 = 0, ph1 = 0;
@@ -1096,17 +987,6 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(ExecArgs a, const VT *yin
         chunk_rows<VT, MT, W, EXACT, DIAG, false>(a, mv, (int32_t)c, lane, yin, yout);
 }
 
-// Per work item: descriptor {item, dep_lo, dep_hi, 0} for the scheduler and
-// the tile's chunk range {c0, c1} for the compute warps.
-__global__ void k_item_info(int32_t n_items, const int32_t *work, const int32_t *dep_lo, const int32_t *dep_hi,
-                            const int32_t *tile_chunk, int4 *desc, int2 *chunks) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_items) return;
-    const int32_t wk = work[j], t = wk >> 8;
-    desc[j] = make_int4(wk, dep_lo[t], dep_hi[t], 0);
-    chunks[j] = make_int2(tile_chunk[t], tile_chunk[t + 1]);
-}
-
 // ---------------------------------------------------------------- Chebyshev
 // Node of a sweep: global power k = k0 + j.  With Ahat = (A - c)/r:
 //   v_1 = Ahat v_0,  v_k = 2 Ahat v_{k-1} - v_{k-2},  acc += coef_k v_k,
@@ -1208,11 +1088,10 @@ struct ChebNode {
                                                     int warp, int nwarps, int lane, const ChebArgs &ca) {
         const Vecs v = vecs(a, ca, j);
         VT acc[kPC][2];
-        int32_t row[kPC];
-        slice_sum<VT, MT, 2>(a, s, v.yin, lane, row, acc);
+        slice_sum<VT, MT, 2>(a, s, v.yin, lane, acc);
 #pragma unroll
         for (int i = 0; i < kPC; i++)
-            if (row[i] >= 0) row_out(a, ca, v, row[i], acc[i][0], acc[i][1]);
+            if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i][0], acc[i][1]);
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
         for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
     }
@@ -1416,19 +1295,6 @@ int wave_occupancy(const Plan *pl, int *ctas_per_sm) {
     return MPK_OK;
 }
 
-size_t pipe_smem_bytes(int val_bytes) { return (size_t)kComputeWarps * 2 * slice_bytes(val_bytes); }
-
-int build_item_info(const Plan *pl, const int32_t *work, int32_t n_items, int4 **desc, int2 **chunks,
-                    cudaStream_t st) {
-    int rc = dev_alloc<int4>(nullptr, desc, (size_t)n_items);
-    if (!rc) rc = dev_alloc<int2>(nullptr, chunks, (size_t)n_items);
-    if (rc) return rc;
-    k_item_info<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(n_items, work, pl->d_dep_lo, pl->d_dep_hi,
-                                                                  pl->d_tile_chunk, *desc, *chunks);
-    MPK_CUDA(cudaGetLastError());
-    return MPK_OK;
-}
-
 ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     ExecArgs a;
     a.chunk_row = pl->d_chunk_row;
@@ -1457,8 +1323,6 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.tile_off = pl->d_tile_off;
     a.row_map = pl->d_row_map;
     a.chunk_rec = pl->d_chunk_rec;
-    a.item_desc = pl->d_item_desc;
-    a.item_chunks = pl->d_item_chunks;
     a.stage_recs = pl->stage_recs;
     a.stage_entries = pl->stage_entries;
     a.tune = pl->tune;
@@ -1710,21 +1574,12 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
                     cudaFree(pl->d_work_rem);
                     pl->d_work_rem = nullptr;
                 }
-                if (pl->d_item_desc_rem) cudaFree(pl->d_item_desc_rem);
-                if (pl->d_item_chunks_rem) cudaFree(pl->d_item_chunks_rem);
-                pl->d_item_desc_rem = nullptr;
-                pl->d_item_chunks_rem = nullptr;
                 if ((rc = dev_alloc<int32_t>(nullptr, &pl->d_work_rem, work.size()))) return rc;
                 MPK_CUDA(cudaMemcpyAsync(pl->d_work_rem, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
-                if ((rc = build_item_info(pl, pl->d_work_rem, (int32_t)work.size(), &pl->d_item_desc_rem,
-                                          &pl->d_item_chunks_rem, st)))
-                    return rc;
                 MPK_CUDA(cudaStreamSynchronize(st));
                 pl->rem_p = pw;
             }
             ca.e.work = pl->d_work_rem;
-            ca.e.item_desc = pl->d_item_desc_rem;
-            ca.e.item_chunks = pl->d_item_chunks_rem;
             ca.e.n_items = pl->n_tiles * pw;
             ca.e.p = pw;
         }

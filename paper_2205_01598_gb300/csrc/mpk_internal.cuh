@@ -71,8 +71,6 @@ struct Plan {
     // host copies kept to build the issue order of shorter sweeps
     std::vector<int32_t> h_tile_row, h_group_tile, h_dep_hi, h_work;
     int32_t *d_work_rem = nullptr;  // issue order for rem_p powers (Chebyshev remainder sweep)
-    int4 *d_item_desc = nullptr, *d_item_desc_rem = nullptr;     // per item {item, dep_lo, dep_hi, 0}
-    int2 *d_item_chunks = nullptr, *d_item_chunks_rem = nullptr; // per item {first chunk, end chunk}
     int32_t rem_p = 0;
 
     std::vector<int32_t> h_level_ptr, h_group_ptr;
@@ -124,8 +122,6 @@ struct ExecArgs {
     uint32_t tune;               // MPK_TUNE_* bits
     const int32_t *row_map;      // chunk position -> row (rows sorted by length in a tile); null = identity
     const int4 *chunk_rec;       // per chunk {first row, rows, first entry / 32, width}
-    const int4 *item_desc;       // per work item {item, dep_lo, dep_hi, 0}
-    const int2 *item_chunks;     // per work item {first chunk, end chunk} of its tile
     int32_t stage_recs;          // chunk records one resident stage holds
 };
 
@@ -189,11 +185,6 @@ double order_items(const Plan *pl, int32_t p_sweep, double lag, std::vector<int3
 int wave_occupancy(const Plan *pl, int *ctas_per_sm);
 const void *batch_kernel(int prec);
 int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st, int threads = kWaveThreads);
-int build_item_info(const Plan *pl, const int32_t *work, int32_t n_items, int4 **desc, int2 **chunks,
-                    cudaStream_t st);
-// Dynamic shared memory of the work-list wavefront's compute warps (two
-// staged slices per warp; see the staged-slice section of mpk_exec.cu).
-size_t pipe_smem_bytes(int val_bytes);
 
 inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
 inline int wave_threads(const Plan *pl) { return pl->resident ? kResThreads : kWaveThreads; }

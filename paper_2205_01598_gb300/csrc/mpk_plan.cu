@@ -580,8 +580,7 @@ void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
                   pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
-                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec, pl->d_item_desc,
-                  pl->d_item_desc_rem, pl->d_item_chunks, pl->d_item_chunks_rem};
+                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec};
     for (void *p : ps)
         if (p) cudaFree(p);
 }
@@ -943,7 +942,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         } else {
             const size_t need = 2 * (size_t)pl->stage_entries * (size_t)(4 + pl->val_bytes);
             pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
-            pl->smem_bytes = pl->staged ? need : pipe_smem_bytes(pl->val_bytes);
+            pl->smem_bytes = pl->staged ? need : 0;
         }
     }
 
@@ -967,7 +966,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             pl->grid_ctas = (int32_t)G;
         } else {
             pl->resident = 0;
-            pl->smem_bytes = pipe_smem_bytes(pl->val_bytes);
+            pl->smem_bytes = 0;
         }
     }
     if (!pl->resident) {
@@ -987,8 +986,6 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         pl->slope = order_items(pl, p, o->lag, work);
         MPK_TRY(dev_alloc(pl, &pl->d_work, work.size()));
         MPK_CUDA(cudaMemcpyAsync(pl->d_work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
-        MPK_TRY(build_item_info(pl, pl->d_work, (int32_t)work.size(), &pl->d_item_desc, &pl->d_item_chunks, st));
-        pl->device_bytes += (int64_t)work.size() * (int64_t)(sizeof(int4) + sizeof(int2));
         MPK_CUDA(cudaStreamSynchronize(st));
         pl->h_work = std::move(work);
     }
