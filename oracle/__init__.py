@@ -70,6 +70,8 @@ def _load():
             lib.oracle_gershgorin.argtypes = [i32, i32p, i32p, f64p, C.POINTER(f64), C.POINTER(f64)]
             lib.oracle_cheb_coeffs_schroedinger.argtypes = [i32, f64, f64, f64, f64p]
             lib.oracle_cheb.argtypes = [i32, i32p, i32p, f64p, f64, f64, i32, f64p, f64p, f64p]
+            lib.oracle_cheb_coeffs_heat.argtypes = [i32, f64, f64, f64, f64p]
+            lib.oracle_cheb_real.argtypes = [i32, i32p, i32p, f64p, f64, f64, i32, f64p, f64p, f64p]
             _lib = lib
     return _lib
 
@@ -189,3 +191,22 @@ def cheb(A, coef, c, r, x):
     y = np.empty((A.n, 2), dtype=np.float64)
     lib.oracle_cheb(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), float(c), float(r), int(M), ci, xi, y)
     return y[:, 0] + 1j * y[:, 1]
+
+
+def cheb_coeffs_heat(M, c, r, tau):
+    """Real coefficients (M+1,) of exp(-tau A) in T_k((A-c)/r) (modified Bessel)."""
+    lib = _load()
+    out = np.empty(M + 1, dtype=np.float64)
+    lib.oracle_cheb_coeffs_heat(int(M), float(c), float(r), float(tau), out)
+    return out
+
+
+def cheb_real(A, coef, c, r, x):
+    """y = sum_k coef_k T_k((A-c)/r) x for real x and coef (Eq. 7-9), FP64."""
+    lib = _load()
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    M = coef.shape[0] - 1
+    y = np.empty(A.n, dtype=np.float64)
+    lib.oracle_cheb_real(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), float(c), float(r), int(M), coef,
+                         _f64(x), y)
+    return y

@@ -301,3 +301,56 @@ void oracle_cheb(int32_t n, const int32_t *rowptr, const int32_t *col, const dou
     }
     free(vprev); free(vcur); free(av);
 }
+
+/* Heat-equation propagator coefficients (Sec. 7, the modified-Bessel case):
+ * with A = c + r*Ahat and tau = a*dt,
+ *   exp(-tau A) = exp(-tau c) [ I_0(tau r) T_0(Ahat) + 2 sum_{k>=1} (-1)^k I_k(tau r) T_k(Ahat) ],
+ * the generating function exp(z cos t) = I_0(z) + 2 sum_k I_k(z) cos(k t) taken at
+ * z = -tau r (I_k(-z) = (-1)^k I_k(z)).  The scaled values I_k(z) e^{-z} come from
+ * the integral (1/pi) int_0^pi exp(z (cos t - 1)) cos(k t) dt, evaluated with the
+ * trapezoid rule on nq panels (exponentially convergent for this periodic,
+ * analytic integrand); exp(-tau c) I_k(z) = exp(-tau (c - r)) * I_k(z) e^{-z}.
+ * coef holds M+1 real numbers. */
+void oracle_cheb_coeffs_heat(int32_t M, double c, double r, double tau, double *coef)
+{
+    const double z = tau * r, pi = acos(-1.0);
+    const int32_t nq = 8192 + 8 * M + (int32_t)(16.0 * sqrt(z + 1.0));
+    const double scale = exp(-tau * (c - r));
+    for (int32_t k = 0; k <= M; k++) {
+        double s = 0.0;
+        for (int32_t j = 0; j <= nq; j++) {
+            const double t = pi * (double)j / (double)nq;
+            const double f = exp(z * (cos(t) - 1.0)) * cos((double)k * t);
+            s += (j == 0 || j == nq) ? 0.5 * f : f;
+        }
+        const double ive = s / (double)nq;
+        coef[k] = (k == 0 ? 1.0 : 2.0) * ((k & 1) ? -1.0 : 1.0) * scale * ive;
+    }
+}
+
+/* Chebyshev time propagation (Sec. 7, Eq. 7-9) for a real matrix A and a
+ * real vector x: Ahat = (A - c I) / r, v_0 = x, v_1 = Ahat v_0,
+ * v_{k+1} = 2 Ahat v_k - v_{k-1}, y = sum_{k=0}^{M} coef_k v_k (coef real).
+ * All arithmetic in FP64. */
+void oracle_cheb_real(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val,
+                      double c, double r, int32_t M, const double *coef, const double *x, double *y)
+{
+    const size_t len = (size_t)(n > 0 ? n : 1);
+    double *vprev = (double *)malloc(sizeof(double) * len);
+    double *vcur  = (double *)malloc(sizeof(double) * len);
+    double *av    = (double *)malloc(sizeof(double) * len);
+    memcpy(vprev, x, sizeof(double) * (size_t)n);
+    for (int32_t i = 0; i < n; i++) y[i] = coef[0] * x[i];
+    for (int32_t k = 1; k <= M; k++) {
+        const double *src = (k == 1) ? vprev : vcur;
+        if (n > 0) oracle_spmv_rows(rowptr, col, val, 1, src, av, 0, n - 1);
+        for (int32_t i = 0; i < n; i++) {
+            double ah = (av[i] - c * src[i]) / r;   /* Ahat v */
+            double vnew = (k == 1) ? ah : 2.0 * ah - vprev[i];
+            if (k > 1) vprev[i] = vcur[i];
+            vcur[i] = vnew;
+        }
+        for (int32_t i = 0; i < n; i++) y[i] += coef[k] * vcur[i];
+    }
+    free(vprev); free(vcur); free(av);
+}
