@@ -225,6 +225,21 @@ int mpk_cheb_coeffs_schroedinger(int32_t M, double c, double r, double dt, doubl
 int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
              const void *x, double *y, uint32_t flags);
 
+/* Host helper: the M+1 real coefficients (HOST memory) of the heat-equation
+ * propagator exp(-tau A) = sum_k coef_k T_k((A - c)/r), tau = a*dt (Sec. 7;
+ * modified-Bessel coefficients): coef_0 = e^{-tau c} I_0(tau r),
+ * coef_k = 2 e^{-tau c} (-1)^k I_k(tau r).  The scaled I_k(z) e^{-z} are
+ * computed by Miller's backward recurrence normalised by
+ * I_0 + 2 sum_k I_k = e^z.  MPK_ERR_INVALID if M < 0, r <= 0 or tau < 0.   */
+int mpk_cheb_coeffs_heat(int32_t M, double c, double r, double tau, double *coef);
+
+/* Real Chebyshev propagation (the heat equation of Sec. 7): as mpk_cheb with
+ * a plan of nrhs = 1, x and v_k real vectors of n entries in the plan
+ * precision, coef M+1 real numbers (HOST memory), and y n DOUBLES.
+ * MPK_ERR_INVALID if nrhs != 1, M < 1 or r == 0.                           */
+int mpk_cheb_real(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
+                  const void *x, double *y, uint32_t flags);
+
 /* ---------------------------------------------------------------- batches
  * Several plans (different matrices, sizes, block widths nrhs and powers p)
  * run in ONE persistent wavefront launch: their issue orders (each the

@@ -122,6 +122,8 @@ def load(path: str | None = None):
             "mpk_gershgorin": ([vp, C.POINTER(f64), C.POINTER(f64)], C.c_int),
             "mpk_cheb_coeffs_schroedinger": ([i32, f64, f64, f64, vp], C.c_int),
             "mpk_cheb": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
+            "mpk_cheb_real": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
+            "mpk_cheb_coeffs_heat": ([i32, f64, f64, f64, vp], C.c_int),
             "mpk_permute_vectors": ([vp, vp, vp, i32, i32, i32], C.c_int),
             "mpk_plan_destroy": ([vp], C.c_int),
             "mpk_strerror": ([C.c_int], C.c_char_p),
@@ -314,6 +316,25 @@ def mpk_cheb_coeffs_schroedinger(M, c, r, dt) -> np.ndarray:
     _check(load().mpk_cheb_coeffs_schroedinger(int(M), float(c), float(r), float(dt),
                                                out.ctypes.data_as(C.c_void_p)), "mpk_cheb_coeffs_schroedinger")
     return out[0::2] + 1j * out[1::2]
+
+
+def mpk_cheb_coeffs_heat(M, c, r, tau) -> np.ndarray:
+    """Real coefficients (M+1,) of exp(-tau A) in T_k((A - c)/r) (mpk_cheb_coeffs_heat)."""
+    out = np.empty(M + 1, dtype=np.float64)
+    _check(load().mpk_cheb_coeffs_heat(int(M), float(c), float(r), float(tau), out.ctypes.data_as(C.c_void_p)),
+           "mpk_cheb_coeffs_heat")
+    return out
+
+
+def mpk_cheb_real(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False, one_power_per_launch=False):
+    """y = sum_k coef_k T_k((A - c)/r) x for real x (n,) in the plan precision
+    and y (n,) float64 CUDA tensors; coef: real host array of length M+1
+    (mpk_cheb_real)."""
+    ci = np.ascontiguousarray(coef, dtype=np.float64)
+    _check(load().mpk_cheb_real(plan.handle, ci.ctypes.data_as(C.c_void_p), ci.shape[0] - 1, float(c), float(r),
+                                _ptr(x), _ptr(y),
+                                _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)),
+           "mpk_cheb_real")
 
 
 def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False, one_power_per_launch=False):

@@ -990,11 +990,13 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(ExecArgs a, const VT *yin
 // ---------------------------------------------------------------- Chebyshev
 // Node of a sweep: global power k = k0 + j.  With Ahat = (A - c)/r:
 //   v_1 = Ahat v_0,  v_k = 2 Ahat v_{k-1} - v_{k-2},  acc += coef_k v_k,
-// vectors complex (two columns re, im) in a ring of three blocks; A v is
-// summed in the storage precision, the scaling, the recurrence update and
-// the coefficient sum are done in FP64.
-template <typename VT, typename MT, bool DIAG>
+// vectors in a ring of three blocks, G columns: G = 2 complex (re, im; the
+// Schroedinger propagator, complex coefficients), G = 1 real (the heat
+// propagator, real coefficients).  A v is summed in the storage precision;
+// the scaling, the recurrence update and the coefficient sum are done in FP64.
+template <typename VT, typename MT, bool DIAG, int G>
 struct ChebNode {
+    static_assert(G == 1 || G == 2, "real or complex vectors");
     static constexpr bool kPipe = true;
 
     struct Vecs {
@@ -1007,33 +1009,31 @@ struct ChebNode {
         const int32_t k = ca.k0 + j;
         VT *ring = (VT *)ca.ring;
         return Vecs{ring + (int64_t)((k - 1) % 3) * a.blk, ring + (int64_t)((k + 1) % 3) * a.blk,   // (k-2) mod 3
-                    ring + (int64_t)(k % 3) * a.blk, ca.coef[2 * k], ca.coef[2 * k + 1], k};
+                    ring + (int64_t)(k % 3) * a.blk, G == 2 ? ca.coef[2 * k] : ca.coef[k],
+                    G == 2 ? ca.coef[2 * k + 1] : 0.0, k};
     }
 
-    // Row r of the sweep step, given (s0, s1) = (A v_{k-1})[r] without a
-    // separately stored diagonal.
+    // Row r of the sweep step, given s = (A v_{k-1})[r] without a separately
+    // stored diagonal.
     __device__ __forceinline__ static void row_out(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
-                                                   VT s0, VT s1) {
-        const double u0 = (double)v.yin[2 * (int64_t)r], u1 = (double)v.yin[2 * (int64_t)r + 1];
-        double a0, a1;
-        if (DIAG) {   // the diagonal term enters in FP64 together with the shift
-            const double d = (double)__ldg(a.diag + r);
-            a0 = ca.alpha * ((double)s0 + d * u0) + ca.beta * u0;
-            a1 = ca.alpha * ((double)s1 + d * u1) + ca.beta * u1;
+                                                   const VT (&s)[G]) {
+        double nv[G];
+        const double d = DIAG ? (double)__ldg(a.diag + r) : 0.0;
+#pragma unroll
+        for (int q = 0; q < G; q++) {
+            const double u = (double)v.yin[G * (int64_t)r + q];
+            // the diagonal term enters in FP64 together with the shift
+            const double ah = DIAG ? ca.alpha * ((double)s[q] + d * u) + ca.beta * u : ca.alpha * (double)s[q] + ca.beta * u;
+            nv[q] = v.k > 1 ? 2.0 * ah - (double)v.yprev[G * (int64_t)r + q] : ah;
+            v.yout[G * (int64_t)r + q] = (VT)nv[q];
+        }
+        double *acc = ca.acc + G * (int64_t)r;
+        if (G == 2) {
+            acc[0] += v.cre * nv[0] - v.cim * nv[G - 1];
+            acc[G - 1] += v.cre * nv[G - 1] + v.cim * nv[0];
         } else {
-            a0 = ca.alpha * (double)s0 + ca.beta * u0;
-            a1 = ca.alpha * (double)s1 + ca.beta * u1;
+            acc[0] += v.cre * nv[0];
         }
-        double n0 = a0, n1 = a1;
-        if (v.k > 1) {
-            n0 = 2.0 * a0 - (double)v.yprev[2 * (int64_t)r];
-            n1 = 2.0 * a1 - (double)v.yprev[2 * (int64_t)r + 1];
-        }
-        v.yout[2 * (int64_t)r] = (VT)n0;
-        v.yout[2 * (int64_t)r + 1] = (VT)n1;
-        double *acc = ca.acc + 2 * (int64_t)r;
-        acc[0] += v.cre * n0 - v.cim * n1;
-        acc[1] += v.cre * n1 + v.cim * n0;
     }
 
     template <bool STAGED>
@@ -1046,7 +1046,9 @@ struct ChebNode {
         const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
         const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
         const int64_t e0 = off + lane;
-        VT s0 = VT(0), s1 = VT(0);
+        VT sum[G];
+#pragma unroll
+        for (int q = 0; q < G; q++) sum[q] = VT(0);
         constexpr int B = 8;
         for (int32_t q0 = 0; q0 < w; q0 += B) {
             int32_t cols[B];
@@ -1058,14 +1060,12 @@ struct ChebNode {
                 vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(q0 + u) * kChunk)) : VT(0);
             }
 #pragma unroll
-            for (int u = 0; u < B; u++) {
-                if (cols[u] >= 0) {
-                    s0 = fma(vals[u], v.yin[2 * (int64_t)cols[u]], s0);
-                    s1 = fma(vals[u], v.yin[2 * (int64_t)cols[u] + 1], s1);
-                }
-            }
+            for (int u = 0; u < B; u++)
+                if (cols[u] >= 0)
+#pragma unroll
+                    for (int q = 0; q < G; q++) sum[q] = fma(vals[u], v.yin[G * (int64_t)cols[u] + q], sum[q]);
         }
-        row_out(a, ca, v, r, s0, s1);
+        row_out(a, ca, v, r, sum);
     }
 
     template <bool STAGED>
@@ -1080,33 +1080,33 @@ struct ChebNode {
                                                    const MT *sval, int64_t ebase, int32_t nch, int32_t j, int warp,
                                                    int nwarps, int lane, const ChebArgs &ca) {
         const Vecs v = vecs(a, ca, j);
-        resident_rows<VT, MT, 2>(a, srec, scol, sval, ebase, nch, warp, nwarps, lane, v.yin,
-                                 [&](int32_t r, const VT (&acc)[2]) { row_out(a, ca, v, r, acc[0], acc[1]); });
+        resident_rows<VT, MT, G>(a, srec, scol, sval, ebase, nch, warp, nwarps, lane, v.yin,
+                                 [&](int32_t r, const VT (&acc)[G]) { row_out(a, ca, v, r, acc); });
     }
 
     __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT> &s, int32_t t, int32_t j,
                                                     int warp, int nwarps, int lane, const ChebArgs &ca) {
         const Vecs v = vecs(a, ca, j);
-        VT acc[kPC][2];
-        slice_sum<VT, MT, 2>(a, s, v.yin, lane, acc);
+        VT acc[kPC][G];
+        slice_sum<VT, MT, G>(a, s, v.yin, lane, acc);
 #pragma unroll
         for (int i = 0; i < kPC; i++)
-            if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i][0], acc[i][1]);
+            if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i]);
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
         for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
     }
 };
 
-template <typename VT, typename MT, bool DIAG, bool STAGED>
+template <typename VT, typename MT, bool DIAG, bool STAGED, int G>
 __global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
     const OnePlan src{ca.e, (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u};
-    wave_loop<ChebNode<VT, MT, DIAG>, MT, STAGED>(ca.e, src, ca);
+    wave_loop<ChebNode<VT, MT, DIAG, G>, MT, STAGED>(ca.e, src, ca);
 }
 
-template <typename VT, typename MT, bool DIAG>
+template <typename VT, typename MT, bool DIAG, int G>
 __global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
     const uint32_t epoch = (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u;
-    resident_loop<ChebNode<VT, MT, DIAG>, MT>(ca.e, epoch, ca);
+    resident_loop<ChebNode<VT, MT, DIAG, G>, MT>(ca.e, epoch, ca);
 }
 
 // ---------------------------------------------------------------- batched MPK
@@ -1142,14 +1142,18 @@ __global__ void __launch_bounds__(kWaveThreads) k_batch_wave(BatchArgs b) {
     wave_loop<BatchNode<VT, MT>, MT, false>(b.g, src, 0);
 }
 
-// acc = coef_0 * v_0 (complex), v_0 = ring block 0
-template <typename VT>
+// acc = coef_0 * v_0 (complex for G = 2, real for G = 1), v_0 = ring block 0
+template <typename VT, int G>
 __global__ void k_cheb_init(int32_t n, const VT *v0, const double *coef, double *acc) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const double x0 = (double)v0[2 * r], x1 = (double)v0[2 * r + 1];
-    acc[2 * r] = coef[0] * x0 - coef[1] * x1;
-    acc[2 * r + 1] = coef[0] * x1 + coef[1] * x0;
+    if (G == 2) {
+        const double x0 = (double)v0[2 * r], x1 = (double)v0[2 * r + 1];
+        acc[2 * r] = coef[0] * x0 - coef[1] * x1;
+        acc[2 * r + 1] = coef[0] * x1 + coef[1] * x0;
+    } else {
+        acc[r] = coef[0] * (double)v0[r];
+    }
 }
 
 // Gershgorin row bounds -> per-block min/max (lo in [2b], hi in [2b+1])
@@ -1232,12 +1236,16 @@ const void *pick_wave_t(const Plan *pl) {
     if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, STAGED>(pl->nrhs);
     return wave_ptr<float, float, true, STAGED>(pl->nrhs);
 }
+template <bool STAGED, int G>
+const void *pick_cheb_g(const Plan *pl) {
+    if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false, STAGED, G>;
+    if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED, G>;
+    if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED, G>;
+    return (const void *)k_cheb_wave<float, float, true, STAGED, G>;
+}
 template <bool STAGED>
 const void *pick_cheb_t(const Plan *pl) {
-    if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false, STAGED>;
-    if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED>;
-    if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED>;
-    return (const void *)k_cheb_wave<float, float, true, STAGED>;
+    return pl->nrhs == 1 ? pick_cheb_g<STAGED, 1>(pl) : pick_cheb_g<STAGED, 2>(pl);
 }
 template <int W>
 const void *pick_res_w(const Plan *pl) {
@@ -1246,12 +1254,14 @@ const void *pick_res_w(const Plan *pl) {
     if (pl->val_bytes == 2) return (const void *)k_res_wave<float, __nv_bfloat16, W, true>;
     return (const void *)k_res_wave<float, float, W, true>;
 }
-const void *pick_res_cheb(const Plan *pl) {
-    if (pl->prec == MPK_F64) return (const void *)k_res_cheb<double, double, false>;
-    if (!pl->has_diag) return (const void *)k_res_cheb<float, float, false>;
-    if (pl->val_bytes == 2) return (const void *)k_res_cheb<float, __nv_bfloat16, true>;
-    return (const void *)k_res_cheb<float, float, true>;
+template <int G>
+const void *pick_res_cheb_g(const Plan *pl) {
+    if (pl->prec == MPK_F64) return (const void *)k_res_cheb<double, double, false, G>;
+    if (!pl->has_diag) return (const void *)k_res_cheb<float, float, false, G>;
+    if (pl->val_bytes == 2) return (const void *)k_res_cheb<float, __nv_bfloat16, true, G>;
+    return (const void *)k_res_cheb<float, float, true, G>;
 }
+const void *pick_res_cheb(const Plan *pl) { return pl->nrhs == 1 ? pick_res_cheb_g<1>(pl) : pick_res_cheb_g<2>(pl); }
 const void *pick_wave(const Plan *pl) {
     if (pl->resident) return pl->nrhs == 1 ? pick_res_w<1>(pl) : pick_res_w<2>(pl);
     return pl->staged ? pick_wave_t<true>(pl) : pick_wave_t<false>(pl);
@@ -1282,7 +1292,7 @@ const void *pick_spmv(const Plan *pl) {
 // dynamic shared memory of the staged form); also raises the kernels' limit
 // of dynamic shared memory to what the plan needs.
 int wave_occupancy(const Plan *pl, int *ctas_per_sm) {
-    const void *fns[2] = {pick_wave(pl), pl->nrhs == 2 ? pick_cheb(pl) : nullptr};
+    const void *fns[2] = {pick_wave(pl), pl->nrhs <= 2 ? pick_cheb(pl) : nullptr};
     int occ = 1 << 30;
     for (const void *fn : fns) {
         if (!fn) continue;
@@ -1514,17 +1524,19 @@ int mpk_gershgorin(mpk_plan_t plan, double *lo, double *hi) {
     return MPK_OK;
 }
 
-int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
-             uint32_t flags) {
+// Chebyshev propagation with G vector columns (2: complex state and
+// coefficients, 1: real); the plan's block width must be G.
+static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
+                    uint32_t flags, int G) {
     if (!plan || !coef || !x || !y || M < 1 || !(r != 0.0)) return MPK_ERR_INVALID;
     Plan *pl = &plan->pl;
-    if (pl->nrhs != 2) return MPK_ERR_INVALID;
+    if (pl->nrhs != G) return MPK_ERR_INVALID;
     cudaStream_t st = pl->stream;
     const int eb = elem_bytes_of(pl);
-    const size_t blk = (size_t)pl->n * 2;
+    const size_t blk = (size_t)pl->n * G;
     // device storage: 3-block ring (storage precision), FP64 accumulator, coefficients
     const size_t ring_b = 3 * blk * eb, acc_b = (flags & MPK_IO_PERMUTED) ? 0 : blk * sizeof(double);
-    const size_t coef_b = sizeof(double) * 2 * ((size_t)M + 1);
+    const size_t coef_b = sizeof(double) * G * ((size_t)M + 1);
     const size_t need = ring_b + acc_b + coef_b + 256;
     if (pl->cheb_bytes < need) {
         if (pl->d_cheb) {
@@ -1551,8 +1563,13 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
         return rc;
     }
     const unsigned nb = (unsigned)((pl->n + 255) / 256);
-    if (eb == 8) k_cheb_init<double><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, acc);
-    else k_cheb_init<float><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef, acc);
+    if (G == 2) {
+        if (eb == 8) k_cheb_init<double, 2><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, acc);
+        else k_cheb_init<float, 2><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef, acc);
+    } else {
+        if (eb == 8) k_cheb_init<double, 1><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, acc);
+        else k_cheb_init<float, 1><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef, acc);
+    }
     MPK_CUDA(cudaGetLastError());
     ChebArgs ca;
     ca.ring = ring;
@@ -1588,12 +1605,22 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
         if ((rc = launch_coop(pick_cheb(pl), pl->grid_ctas, pl->smem_bytes, args, st, wave_threads(pl)))) return rc;
     }
     if (!(flags & MPK_IO_PERMUTED)) {
-        // acc (level order, n x 2 doubles) -> y (original order)
+        // acc (level order, n x G doubles) -> y (original order)
         if ((rc = permute_vectors(pl, acc, y, 1, 8, 0, st))) return rc;
     }
     MPK_CUDA(cudaGetLastError());
     if (flags & MPK_ASYNC) return MPK_OK;
     return read_device_error(pl, st);
+}
+
+int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
+             uint32_t flags) {
+    return cheb_run(plan, coef, M, c, r, x, y, flags, 2);
+}
+
+int mpk_cheb_real(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
+                  uint32_t flags) {
+    return cheb_run(plan, coef, M, c, r, x, y, flags, 1);
 }
 
 int mpk_plan_last_error(mpk_plan_t plan, int32_t *code, int32_t *power, int32_t *tile) {
@@ -1618,6 +1645,40 @@ int mpk_plan_debug_drop_flag(mpk_plan_t plan, int32_t tile, int32_t power) {
     if (tile >= pl->n_tiles || power < 1 || power > pl->p) return MPK_ERR_INVALID;
     pl->drop_tile = tile;
     pl->drop_k = power;
+    return MPK_OK;
+}
+
+int mpk_cheb_coeffs_heat(int32_t M, double c, double r, double tau, double *coef) {
+    if (M < 0 || !coef || !(r > 0.0) || !(tau >= 0.0)) return MPK_ERR_INVALID;
+    // exp(-tau c) (2 - delta_k0) (-1)^k I_k(tau r).  The scaled values
+    // I_k(z) e^{-z} come from Miller's backward recurrence
+    // I_{k-1} = I_{k+1} + (2k/z) I_k, started far above the wanted orders with
+    // arbitrary small values and normalised by e^z = I_0 + 2 sum_{k>=1} I_k.
+    const double z = tau * r;
+    std::vector<double> ik((size_t)M + 1, 0.0);
+    if (z == 0.0) {
+        ik[0] = 1.0;
+    } else {
+        const int32_t top = std::max<int32_t>(M, (int32_t)std::ceil(10.0 * std::sqrt(z) + z / 4.0)) + 48;
+        double hi = 0.0, cur = 1e-300, sum = 0.0;   // I_{k+1}, I_k (unnormalised)
+        for (int32_t k = top; k >= 1; k--) {
+            const double lo = hi + (2.0 * k / z) * cur;   // I_{k-1}
+            hi = cur;
+            cur = lo;
+            sum += 2.0 * hi;                            // 2 I_k
+            if (k - 1 <= M) ik[(size_t)(k - 1)] = cur;
+            if (cur > 1e250) {                           // rescale to stay in range
+                for (int32_t q = k - 1; q <= M; q++) ik[(size_t)q] *= 1e-250;
+                hi *= 1e-250;
+                cur *= 1e-250;
+                sum *= 1e-250;
+            }
+        }
+        sum += cur;   // + I_0
+        for (int32_t q = 0; q <= M; q++) ik[(size_t)q] /= sum;
+    }
+    const double scale = std::exp(-tau * (c - r));
+    for (int32_t k = 0; k <= M; k++) coef[k] = (k == 0 ? 1.0 : 2.0) * ((k & 1) ? -1.0 : 1.0) * scale * ik[(size_t)k];
     return MPK_OK;
 }
 
