@@ -113,8 +113,17 @@ __device__ __forceinline__ void chunk_rows(const ExecArgs &a, const MatView<MT, 
     const int nrhs = EXACT ? W : a.nrhs;
     const int64_t e0 = off + lane;
     // B entries of the row are fetched together (indices and values first,
-    // then the B gathers) so that each lane keeps many loads in flight.
-    constexpr int B = W <= 2 ? MPK_BATCH : (W <= 4 ? 4 : 2);
+    // then the B gathers) so that each lane keeps many loads in flight.  When
+    // the block width allows, a row of the block vector is gathered with
+    // 16-byte loads (VEC values each) and B is raised so that about 32 FP32
+    // values' worth of gathers are in flight per lane.
+    constexpr int VEC = 16 / (int)sizeof(VT);
+    constexpr bool CAN_VEC = W % VEC == 0;
+    constexpr int BV = 128 / (W * (int)sizeof(VT)) < 2 ? 2 : (128 / (W * (int)sizeof(VT)) > 8 ? 8 : 128 / (W * (int)sizeof(VT)));
+    constexpr int B = CAN_VEC ? BV : (W <= 2 ? MPK_BATCH : (W <= 4 ? 4 : 2));
+    // vectors only when every VEC group lies inside a row of the block vector
+    const bool vec = CAN_VEC && (EXACT || nrhs % VEC == 0);
+    using V = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
     for (int cb = 0; cb < nrhs; cb += W) {
         VT acc[W];
 #pragma unroll
@@ -128,13 +137,34 @@ __device__ __forceinline__ void chunk_rows(const ExecArgs &a, const MatView<MT, 
                 cols[u] = in ? mv.c(e0 + (int64_t)(j0 + u) * kChunk) : -1;
                 vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(j0 + u) * kChunk)) : VT(0);
             }
+            if (CAN_VEC && vec) {
+                VT g[B][W];
 #pragma unroll
-            for (int u = 0; u < B; u++) {
-                if (cols[u] >= 0) {
-                    const VT *src = yin + (int64_t)cols[u] * nrhs + cb;
+                for (int u = 0; u < B; u++)
 #pragma unroll
-                    for (int i = 0; i < W; i++)
-                        if (EXACT || cb + i < nrhs) acc[i] = fma(vals[u], src[i], acc[i]);
+                    for (int q = 0; q < W / VEC; q++) {
+                        V t;
+                        if (cols[u] >= 0 && (EXACT || cb + q * VEC < nrhs))
+                            t = *reinterpret_cast<const V *>(yin + (int64_t)cols[u] * nrhs + cb + q * VEC);
+                        else
+                            memset(&t, 0, sizeof(t));
+                        memcpy(&g[u][q * VEC], &t, sizeof(t));
+                    }
+#pragma unroll
+                for (int u = 0; u < B; u++)
+                    if (cols[u] >= 0)
+#pragma unroll
+                        for (int i = 0; i < W; i++)
+                            if (EXACT || cb + i < nrhs) acc[i] = fma(vals[u], g[u][i], acc[i]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < B; u++) {
+                    if (cols[u] >= 0) {
+                        const VT *src = yin + (int64_t)cols[u] * nrhs + cb;
+#pragma unroll
+                        for (int i = 0; i < W; i++)
+                            if (EXACT || cb + i < nrhs) acc[i] = fma(vals[u], src[i], acc[i]);
+                    }
                 }
             }
         }
