@@ -375,28 +375,29 @@ __device__ __forceinline__ void warp_chunks_staged(const ExecArgs &a, const MatV
 constexpr int kPC = MPK_PIPE_CHUNKS;    // chunks of a warp held in registers
 constexpr int kPE = MPK_PIPE_ENTRIES;   // entries of a row held in registers
 
-template <typename MT>
+template <typename MT, int PC>
 struct Slice {
-    int4 rec[kPC];           // {first row, rows, first entry / 32, width}; rows 0 = no chunk
-    int32_t row[kPC];        // output row of this lane, -1 = none
-    int32_t col[kPC][kPE];   // -1 = past the row's end
-    MT val[kPC][kPE];
+    int4 rec[PC];            // {first row, rows, first entry / 32, width}; rows 0 = no chunk
+    int32_t row[PC];         // output row of this lane, -1 = none
+    int32_t col[PC][kPE];    // -1 = past the row's end
+    MT val[PC][kPE];
     int32_t c0, c1;          // chunk range of the item's tile
 };
 
+template <int PC>
 __device__ __forceinline__ void slice_recs(const ExecArgs &a, int32_t c0, int32_t c1, int warp, int ncw,
-                                           int4 (&rec)[kPC]) {
+                                           int4 (&rec)[PC]) {
 #pragma unroll
-    for (int i = 0; i < kPC; i++) {
+    for (int i = 0; i < PC; i++) {
         const int32_t c = c0 + warp + i * ncw;
         rec[i] = c < c1 ? __ldg(a.chunk_rec + c) : make_int4(0, 0, 0, 0);
     }
 }
 
-template <typename MT>
-__device__ __forceinline__ void slice_entries(const ExecArgs &a, Slice<MT> &s, int lane) {
+template <typename MT, int PC>
+__device__ __forceinline__ void slice_entries(const ExecArgs &a, Slice<MT, PC> &s, int lane) {
 #pragma unroll
-    for (int i = 0; i < kPC; i++) {
+    for (int i = 0; i < PC; i++) {
         const int4 r = s.rec[i];
         const bool on = lane < r.y;
         s.row[i] = on ? (a.row_map ? __ldg(a.row_map + r.x + lane) : r.x + lane) : -1;
@@ -413,22 +414,22 @@ __device__ __forceinline__ void slice_entries(const ExecArgs &a, Slice<MT> &s, i
 // acc[i][q] = sum over the entries of the lane's row in held chunk i of
 // value * yin[col * G + q], in entry order (the order of chunk_rows, so both
 // paths round alike).  All gathers of the held entries are issued first.
-template <typename VT, typename MT, int G>
-__device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT> &s, const VT *yin, int lane,
-                                          VT (&acc)[kPC][G]) {
-    VT g[kPC][kPE][G];
+template <typename VT, typename MT, int G, int PC>
+__device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT, PC> &s, const VT *yin, int lane,
+                                          VT (&acc)[PC][G]) {
+    VT g[PC][kPE][G];
 #pragma unroll
-    for (int i = 0; i < kPC; i++)
+    for (int i = 0; i < PC; i++)
 #pragma unroll
         for (int u = 0; u < kPE; u++)
 #pragma unroll
             for (int q = 0; q < G; q++) g[i][u][q] = s.col[i][u] >= 0 ? yin[(int64_t)s.col[i][u] * G + q] : VT(0);
 #pragma unroll
-    for (int i = 0; i < kPC; i++)
+    for (int i = 0; i < PC; i++)
 #pragma unroll
         for (int q = 0; q < G; q++) acc[i][q] = VT(0);
 #pragma unroll
-    for (int i = 0; i < kPC; i++)
+    for (int i = 0; i < PC; i++)
 #pragma unroll
         for (int u = 0; u < kPE; u++)
             if (s.col[i][u] >= 0) {
@@ -438,7 +439,7 @@ __device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT> &s,
             }
     // entries past the held ones (rows wider than kPE)
 #pragma unroll
-    for (int i = 0; i < kPC; i++) {
+    for (int i = 0; i < PC; i++) {
         const int32_t w = s.rec[i].w;
         if (s.row[i] < 0 || w <= kPE) continue;
         const int64_t e0 = (int64_t)s.rec[i].z * kChunk + lane;
@@ -529,15 +530,15 @@ template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
 struct MpkNode {
     static constexpr bool kPipe = W == 1 && EXACT;   // single vectors run from register-held slices
 
-    template <typename Extra>
-    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT> &s, int32_t t, int32_t k,
+    template <typename Extra, int PC>
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT, PC> &s, int32_t t, int32_t k,
                                                     int warp, int nwarps, int lane, const Extra &) {
         const VT *yin = k == 1 ? (const VT *)a.x : (const VT *)a.Y + (int64_t)(k - 2) * a.blk;
         VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
-        VT acc[kPC][1];
-        slice_sum<VT, MT, 1>(a, s, yin, lane, acc);
+        VT acc[PC][1];
+        slice_sum<VT, MT, 1, PC>(a, s, yin, lane, acc);
 #pragma unroll
-        for (int i = 0; i < kPC; i++) {
+        for (int i = 0; i < PC; i++) {
             const int32_t r = s.row[i];
             if (r < 0) continue;
             VT v = acc[i][0];
@@ -545,7 +546,7 @@ struct MpkNode {
             yout[r] = v;
         }
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
-        for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps)
+        for (int32_t c = s.c0 + warp + PC * nwarps; c < s.c1; c += nwarps)
             chunk_rows<VT, MT, 1, true, DIAG, false>(a, mv, c, lane, yin, yout);
     }
 
@@ -634,7 +635,7 @@ struct ManyPlans {
 // slice in registers (Slice): they know which item comes next because the
 // dealing is static -- the scheduler hands them items blockIdx.x,
 // blockIdx.x + gridDim.x, ... in that order, or -1 to stop.
-template <typename Node, typename MT, bool STAGED, typename Src, typename Extra>
+template <typename Node, typename MT, bool STAGED, typename Src, typename Extra, int PC = kPC>
 __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, const Extra &extra) {
     extern __shared__ __align__(128) unsigned char dsmem[];
     __shared__ int s_item, s_stage, s_plan;
@@ -764,7 +765,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
                 c1 = __ldg(a.tile_chunk + t + 1);
             }
         };
-        Slice<MT> s;
+        Slice<MT, PC> s;
         range(j, s.c0, s.c1);
         slice_recs(a, s.c0, s.c1, warp, ncw, s.rec);
         slice_entries(a, s, lane);
@@ -774,15 +775,15 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             named_sync(kBarReady, nthr);
             const int32_t wk = *(volatile int *)&s_item;
             if (wk < 0) break;
-            int4 rn[kPC];   // records of item j + G, and the chunk range of item j + 2G
+            int4 rn[PC];   // records of item j + G, and the chunk range of item j + 2G
             slice_recs(a, n0, n1, warp, ncw, rn);
             int32_t m0, m1;
             range(j + 2 * G, m0, m1);
-            Node::pipe_run(a, s, wk >> 8, wk & 255, warp, ncw, lane, extra);
+            Node::template pipe_run<Extra, PC>(a, s, wk >> 8, wk & 255, warp, ncw, lane, extra);
             s.c0 = n0;
             s.c1 = n1;
 #pragma unroll
-            for (int i = 0; i < kPC; i++) s.rec[i] = rn[i];
+            for (int i = 0; i < PC; i++) s.rec[i] = rn[i];
             slice_entries(a, s, lane);   // item j + G, used after its release
             n0 = m0;
             n1 = m1;
@@ -996,14 +997,17 @@ __global__ void __launch_bounds__(kResThreads) k_res_wave(ExecArgs a) {
 }
 
 #if MPK_WAVE_MIN_BLOCKS > 0
-#define MPK_WAVE_BOUNDS __launch_bounds__(kWaveThreads, MPK_WAVE_MIN_BLOCKS)
+#define MPK_WAVE_BOUNDS(threads) __launch_bounds__(threads, MPK_WAVE_MIN_BLOCKS)
 #else
-#define MPK_WAVE_BOUNDS __launch_bounds__(kWaveThreads)
+#define MPK_WAVE_BOUNDS(threads) __launch_bounds__(threads)
 #endif
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED>
-__global__ void MPK_WAVE_BOUNDS k_wave(ExecArgs a) {
+// NW compute warps per CTA; with 16 of them a warp holds one chunk of a
+// 512-row item (more warps, fewer registers each: the FP64 form, whose
+// FP64 pipe wants more independent rows in flight), with 8 it holds two.
+template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED, int NW>
+__global__ void MPK_WAVE_BOUNDS((NW + 1) * 32) k_wave(ExecArgs a) {
     const OnePlan src{a, (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u};
-    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED>(a, src, 0);
+    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED, OnePlan, int, (NW >= 16 ? 1 : kPC)>(a, src, 0);
 }
 
 // Baseline: one SpMV over all chunks (warp per chunk, grid-stride).
@@ -1114,16 +1118,17 @@ struct ChebNode {
                                  [&](int32_t r, const VT (&acc)[G]) { row_out(a, ca, v, r, acc); });
     }
 
-    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT> &s, int32_t t, int32_t j,
-                                                    int warp, int nwarps, int lane, const ChebArgs &ca) {
+    template <typename Extra, int PC>
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT, PC> &s, int32_t t, int32_t j,
+                                                    int warp, int nwarps, int lane, const Extra &ca) {
         const Vecs v = vecs(a, ca, j);
-        VT acc[kPC][G];
-        slice_sum<VT, MT, G>(a, s, v.yin, lane, acc);
+        VT acc[PC][G];
+        slice_sum<VT, MT, G, PC>(a, s, v.yin, lane, acc);
 #pragma unroll
-        for (int i = 0; i < kPC; i++)
+        for (int i = 0; i < PC; i++)
             if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i]);
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
-        for (int32_t c = s.c0 + warp + kPC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
+        for (int32_t c = s.c0 + warp + PC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
     }
 };
 
@@ -1145,8 +1150,8 @@ __global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
 template <typename VT, typename MT>
 struct BatchNode {
     static constexpr bool kPipe = false;
-    template <typename Extra>
-    __device__ __forceinline__ static void pipe_run(const ExecArgs &, const Slice<MT> &, int32_t, int32_t, int, int,
+    template <typename Extra, int PC>
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &, const Slice<MT, PC> &, int32_t, int32_t, int, int,
                                                     int, const Extra &) {}
 
     template <bool STAGED>
@@ -1238,14 +1243,14 @@ __global__ void k_permute(int32_t n, int32_t words, int32_t count, const int32_t
 }
 
 // ---------------------------------------------------------------- dispatch
-template <typename VT, typename MT, bool DIAG, bool STAGED>
+template <typename VT, typename MT, bool DIAG, bool STAGED, int NW = kComputeWarps>
 const void *wave_ptr(int nrhs) {
     switch (nrhs) {
-    case 1: return (const void *)k_wave<VT, MT, 1, true, DIAG, STAGED>;
-    case 2: return (const void *)k_wave<VT, MT, 2, true, DIAG, STAGED>;
-    case 4: return (const void *)k_wave<VT, MT, 4, true, DIAG, STAGED>;
-    case 8: return (const void *)k_wave<VT, MT, 8, true, DIAG, STAGED>;
-    default: return (const void *)k_wave<VT, MT, 8, false, DIAG, STAGED>;
+    case 1: return (const void *)k_wave<VT, MT, 1, true, DIAG, STAGED, NW>;
+    case 2: return (const void *)k_wave<VT, MT, 2, true, DIAG, STAGED, NW>;
+    case 4: return (const void *)k_wave<VT, MT, 4, true, DIAG, STAGED, NW>;
+    case 8: return (const void *)k_wave<VT, MT, 8, true, DIAG, STAGED, NW>;
+    default: return (const void *)k_wave<VT, MT, 8, false, DIAG, STAGED, NW>;
     }
 }
 template <typename VT, typename MT, bool DIAG>
@@ -1261,7 +1266,7 @@ const void *spmv_ptr(int nrhs) {
 
 template <bool STAGED>
 const void *pick_wave_t(const Plan *pl) {
-    if (pl->prec == MPK_F64) return wave_ptr<double, double, false, STAGED>(pl->nrhs);
+    if (pl->prec == MPK_F64) return wave_ptr<double, double, false, STAGED, STAGED ? kComputeWarps : kFp64Warps>(pl->nrhs);
     if (!pl->has_diag) return wave_ptr<float, float, false, STAGED>(pl->nrhs);
     if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, STAGED>(pl->nrhs);
     return wave_ptr<float, float, true, STAGED>(pl->nrhs);
@@ -1318,20 +1323,21 @@ const void *pick_spmv(const Plan *pl) {
 
 }  // namespace
 
-// Resident CTAs per SM of the wavefront kernels of this plan (with the
-// dynamic shared memory of the staged form); also raises the kernels' limit
-// of dynamic shared memory to what the plan needs.
-int wave_occupancy(const Plan *pl, int *ctas_per_sm) {
+// Resident CTAs per SM of the plan's MPK wavefront kernel and of its
+// Chebyshev kernel (with the plan's dynamic shared memory; 1 << 30 when the
+// plan has no Chebyshev kernel); also raises the kernels' limit of dynamic
+// shared memory to what the plan needs.
+int wave_occupancy(const Plan *pl, int *wave_ctas, int *cheb_ctas) {
     const void *fns[2] = {pick_wave(pl), pl->nrhs <= 2 ? pick_cheb(pl) : nullptr};
-    int occ = 1 << 30;
-    for (const void *fn : fns) {
-        if (!fn) continue;
-        MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes));
-        int o = 0;
-        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, wave_threads(pl), pl->smem_bytes));
-        occ = std::min(occ, o);
+    const int threads[2] = {wave_threads(pl), cheb_threads(pl)};
+    int occ[2] = {1 << 30, 1 << 30};
+    for (int i = 0; i < 2; i++) {
+        if (!fns[i]) continue;
+        MPK_CUDA(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes));
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[i], fns[i], threads[i], pl->smem_bytes));
     }
-    *ctas_per_sm = occ;
+    *wave_ctas = occ[0];
+    *cheb_ctas = occ[1];
     return MPK_OK;
 }
 
@@ -1632,7 +1638,7 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
         }
         ca.k0 = k0;
         void *args[] = {(void *)&ca};
-        if ((rc = launch_coop(pick_cheb(pl), pl->grid_ctas, pl->smem_bytes, args, st, wave_threads(pl)))) return rc;
+        if ((rc = launch_coop(pick_cheb(pl), pl->cheb_grid, pl->smem_bytes, args, st, cheb_threads(pl)))) return rc;
     }
     if (!(flags & MPK_IO_PERMUTED)) {
         // acc (level order, n x G doubles) -> y (original order)

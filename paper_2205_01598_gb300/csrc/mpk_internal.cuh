@@ -20,6 +20,7 @@ constexpr int kMaxNrhs = 64;
 #define MPK_COMPUTE_WARPS 8
 #endif
 constexpr int kComputeWarps = MPK_COMPUTE_WARPS;         // warps that compute work items
+constexpr int kFp64Warps = 16;                           // compute warps of the FP64 MPK wavefront
 constexpr int kWaveThreads = (kComputeWarps + 1) * 32;   // plus one scheduler warp
 constexpr int kSpmvThreads = 256;                        // baseline SpMV CTA
 #ifndef MPK_RES_WARPS
@@ -62,6 +63,8 @@ struct Plan {
     int32_t staged = 0;             // matrix slices staged in shared memory by bulk copies
     int32_t sorted = 0;             // rows of each tile packed in order of decreasing length
     int32_t resident = 0;           // resident schedule (a CTA keeps a tile's slice for all powers)
+    int32_t wave_warps = kComputeWarps;   // compute warps of the MPK wavefront kernel
+    int32_t cheb_grid = 0;          // CTAs of the Chebyshev wavefront launch
     int32_t dep_span = 0;           // max over tiles of dep_hi[t] - t
     int32_t stage_recs = 0;         // chunk records one resident stage holds
     int32_t max_row_len = 0;        // longest row of P A P^T
@@ -182,12 +185,13 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y);
 int ensure_io(Plan *pl, size_t bytes);
 // Issue order of the (tile, power) items for powers 1..p_sweep (mpk_plan.cu).
 double order_items(const Plan *pl, int32_t p_sweep, double lag, std::vector<int32_t> &work);
-int wave_occupancy(const Plan *pl, int *ctas_per_sm);
+int wave_occupancy(const Plan *pl, int *wave_ctas, int *cheb_ctas);
 const void *batch_kernel(int prec);
 int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st, int threads = kWaveThreads);
 
 inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
-inline int wave_threads(const Plan *pl) { return pl->resident ? kResThreads : kWaveThreads; }
+inline int wave_threads(const Plan *pl) { return pl->resident ? kResThreads : (pl->wave_warps + 1) * 32; }
+inline int cheb_threads(const Plan *pl) { return pl->resident ? kResThreads : kWaveThreads; }
 
 }  // namespace mpk
 

@@ -944,6 +944,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
             pl->smem_bytes = pl->staged ? need : 0;
         }
+        pl->wave_warps = (pl->prec == MPK_F64 && !pl->staged && !pl->resident) ? kFp64Warps : kComputeWarps;
     }
 
     // 11. grid size, then the work list: a skewed diagonal order of the Lp
@@ -957,26 +958,30 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         // resident schedule: res_per_sm CTAs per SM, each owning whole tiles;
         // the wait chains cannot close when G > (p-1) * span (or every tile
         // has its own CTA)
-        int occ = 0;
-        MPK_TRY(wave_occupancy(pl, &occ));
+        int occ_w = 0, occ_c = 0;
+        MPK_TRY(wave_occupancy(pl, &occ_w, &occ_c));
         const int64_t G = std::min<int64_t>((int64_t)pl->num_sms * res_per_sm, pl->n_tiles);
         const bool acyclic = G >= pl->n_tiles || G > (int64_t)(p - 1) * pl->dep_span;
-        if (occ >= res_per_sm && acyclic) {
+        if (std::min(occ_w, occ_c) >= res_per_sm && acyclic) {
             pl->ctas_per_sm = res_per_sm;
-            pl->grid_ctas = (int32_t)G;
+            pl->grid_ctas = pl->cheb_grid = (int32_t)G;
         } else {
             pl->resident = 0;
             pl->smem_bytes = 0;
+            pl->wave_warps = pl->prec == MPK_F64 ? kFp64Warps : kComputeWarps;
         }
     }
     if (!pl->resident) {
-        int occ = 0;
-        MPK_TRY(wave_occupancy(pl, &occ));
-        int per_sm = o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : occ;
-        pl->ctas_per_sm = std::max(1, per_sm);
+        int occ_w = 0, occ_c = 0;
+        MPK_TRY(wave_occupancy(pl, &occ_w, &occ_c));
         const int64_t items = (int64_t)pl->n_tiles * p;
-        pl->grid_ctas =
-            (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)pl->num_sms * pl->ctas_per_sm, items));
+        auto grid_of = [&](int occ) {
+            const int per_sm = std::max(1, o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ) : occ);
+            return (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)pl->num_sms * per_sm, items));
+        };
+        pl->ctas_per_sm = std::max(1, o->ctas_per_sm > 0 ? std::min(o->ctas_per_sm, occ_w) : occ_w);
+        pl->grid_ctas = grid_of(occ_w);
+        pl->cheb_grid = occ_c < (1 << 30) ? grid_of(occ_c) : pl->grid_ctas;
     }
     {
         pl->h_tile_row = tile_row;
