@@ -323,6 +323,18 @@ def main():
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": peak_src}
 
+    # the two HBM bounds of the method: p back-to-back SpMVs streaming the
+    # matrix p times, and one read of the matrix per MPK
+    vb = 8 if prec == "f64" else 4
+    bytes_pxspmv = p * (info["nnz"] * (vb + 4) + 4 * A.n + 2 * vb * A.n)
+    bytes_one_read = info["nnz"] * (vb + 4) + 4 * (A.n + 1) + vb * A.n * (1 + p)
+    gbs = peaks["hbm_gbs"] * 1e9
+    bounds = {"pxspmv_hbm_gflops": round(flops / (bytes_pxspmv / gbs) / 1e9, 1),
+              "one_read_hbm_gflops": round(flops / (bytes_one_read / gbs) / 1e9, 1),
+              "frac_of_pxspmv_bound": round(value / (flops / (bytes_pxspmv / gbs) / 1e9), 4),
+              "frac_of_one_read_bound": round(value / (flops / (bytes_one_read / gbs) / 1e9), 4),
+              "dram_bytes_per_nnz_per_power": round(traffic / (info["nnz"] * p), 3) if traffic else None,
+              "hbm_gbs": peaks["hbm_gbs"], "peak_source": peak_src}
     cpu = None
     if rank == 0 and not args.no_cpu:
         gf, reps, el = time_oracle(A, x_host, p)
@@ -352,6 +364,7 @@ def main():
                 "d2h_bytes_per_step": p * A.n * Y.element_size(), "ms_per_step": round(ms_e2e, 4)},
         "gpu_launches": args.steps,
         "roofline": roof,
+        "bounds": bounds,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "plan": {"ms": round(info["plan_ms"], 2), "spmv_equiv": round(info["plan_ms"] / (ms_base / p), 1),
