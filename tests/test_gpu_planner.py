@@ -105,4 +105,4 @@ def test_planner_beats_default(lib):
     r_mlp = P.regret(MS, net.choose(F))
     r_def = P.regret(MS, np.zeros(len(MS), dtype=int))
     assert r_mlp.mean() <= r_def.mean(), (r_mlp, r_def)
-    assert np.median(r_mlp) <= 0.25, r_mlp
+    assert r_mlp.mean() <= 0.10, r_mlp   # within 10 % of the autotuner's best on average
