@@ -495,6 +495,8 @@ def run_cheb(args, kind, size, p, prec, cfg):
     plan = mpk.mpk_plan(rp, cl, va, p, prec=prec, nrhs=G)
     info = mpk.mpk_plan_info(plan)
     lo, hi = mpk.mpk_gershgorin(plan)
+    if heat:   # -Delta is positive semi-definite: spectrum in [0, hi]
+        lo = max(lo, 0.0)
     c, r = (hi + lo) / 2, (hi - lo) / 2
     vdt = torch.float64 if prec == "f64" else torch.float32
     perm = mpk.mpk_plan_perm(plan)[0].long()
@@ -613,6 +615,8 @@ def run_reference(args, kind, size, p, cfg):
     cfg["n"], cfg["nnz"] = A.n, A.nnz
     if kind in ("anderson3d", "heat"):   # Chebyshev configs: one propagation step per step
         lo, hi = oracle.gershgorin(A)
+        if kind == "heat":   # -Delta is positive semi-definite: spectrum in [0, hi]
+            lo = max(lo, 0.0)
         c, r = (hi + lo) / 2, (hi - lo) / 2
         cols = 1 if kind == "heat" else 2
         if kind == "heat":

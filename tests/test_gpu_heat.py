@@ -36,7 +36,11 @@ def _heat(A, prec, p, M, tune=0, permuted=False, one=False, rtau=50.0):
     lo, hi = mpk.mpk_gershgorin(plan)
     if prec == "f64":   # same bounds up to the order of the row sums
         assert abs(lo - olo) <= 1e-14 * max(1.0, abs(olo)) and abs(hi - ohi) <= 1e-14 * max(1.0, abs(ohi))
+    # -Delta of any order is positive semi-definite: its spectrum lies in
+    # [0, hi], tighter than Gershgorin's lower bound for the wider stencils
+    olo = max(olo, 0.0)
     c, r = (ohi + olo) / 2, (ohi - olo) / 2
+    assert abs(np.abs(oracle.cheb_coeffs_heat(M, c, r, rtau / r)).sum() - 1.0) < 1e-12
     coef = oracle.cheb_coeffs_heat(M, c, r, rtau / r)
     x = mi.random_vector(A.n, 77)
     ref = oracle.cheb_real(A, coef, c, r, x)
