@@ -101,7 +101,7 @@ struct MatView {
 // one row per lane (Fig. 1, restricted to the chunk's row range).  W columns
 // of the row-major block vectors are done per pass; EXACT means nrhs == W.
 // Padding entries (column -1) sit at the end of each row and are skipped.
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED>
+template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED, int GB = 32>
 __device__ __forceinline__ void chunk_rows(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t c, int lane,
                                            const VT *yin, VT *yout) {
     const int32_t row0 = __ldg(a.chunk_row + c);
@@ -115,11 +115,13 @@ __device__ __forceinline__ void chunk_rows(const ExecArgs &a, const MatView<MT, 
     // B entries of the row are fetched together (indices and values first,
     // then the B gathers) so that each lane keeps many loads in flight.  When
     // the block width allows, a row of the block vector is gathered with
-    // 16-byte loads (VEC values each) and B is raised so that about 32 FP32
-    // values' worth of gathers are in flight per lane.
+    // 16-byte loads (VEC values each) and B is set so that about GB FP32
+    // values' worth of gathers are in flight per lane (fewer in kernels that
+    // must keep registers low for occupancy).
     constexpr int VEC = 16 / (int)sizeof(VT);
-    constexpr bool CAN_VEC = W % VEC == 0;
-    constexpr int BV = 128 / (W * (int)sizeof(VT)) < 2 ? 2 : (128 / (W * (int)sizeof(VT)) > 8 ? 8 : 128 / (W * (int)sizeof(VT)));
+    constexpr bool CAN_VEC = W % VEC == 0 && GB > 0;   // GB = 0: scalar gathers only
+    constexpr int BW = GB * 4 / (W * (int)sizeof(VT));
+    constexpr int BV = BW < 2 ? 2 : (BW > 8 ? 8 : BW);
     constexpr int B = CAN_VEC ? BV : (W <= 2 ? MPK_BATCH : (W <= 4 ? 4 : 2));
     // vectors only when every VEC group lies inside a row of the block vector
     const bool vec = CAN_VEC && (EXACT || nrhs % VEC == 0);
@@ -526,7 +528,7 @@ __device__ __forceinline__ void resident_rows(const ExecArgs &a, const int4 *sre
 }
 
 // Body of one work item (tile t, power k) of the plain MPK.
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG>
+template <typename VT, typename MT, int W, bool EXACT, bool DIAG, int GB = 32>
 struct MpkNode {
     static constexpr bool kPipe = W == 1 && EXACT;   // single vectors run from register-held slices
 
@@ -578,7 +580,7 @@ struct MpkNode {
             warp_chunks_staged<VT, MT, DIAG>(a, mv, __ldg(a.tile_chunk + t) + warp, c1, nwarps, lane, yin, yout);
         } else {
             for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps)
-                chunk_rows<VT, MT, W, EXACT, DIAG, STAGED>(a, mv, c, lane, yin, yout);
+                chunk_rows<VT, MT, W, EXACT, DIAG, STAGED, GB>(a, mv, c, lane, yin, yout);
         }
     }
 };
@@ -1147,6 +1149,11 @@ __global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
 // ---------------------------------------------------------------- batched MPK
 // Plans of a batch may differ in block width and number of powers; the node
 // dispatches on the plan's nrhs.
+// Gather budget of the batch's row kernel: 16-byte gathers of 16 values in
+// FP32; scalar gathers in FP64 (fits the batch kernel's register budget).
+template <typename VT>
+constexpr int batch_gather_budget() { return sizeof(VT) == 4 ? 16 : 0; }
+
 template <typename VT, typename MT>
 struct BatchNode {
     static constexpr bool kPipe = false;
@@ -1157,18 +1164,24 @@ struct BatchNode {
     template <bool STAGED>
     __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t k,
                                                int warp, int nwarps, int lane, const int &x) {
+        constexpr int GB = batch_gather_budget<VT>();
         switch (a.nrhs) {
-        case 1: MpkNode<VT, MT, 1, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
-        case 2: MpkNode<VT, MT, 2, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
-        case 4: MpkNode<VT, MT, 4, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
-        case 8: MpkNode<VT, MT, 8, true, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
-        default: MpkNode<VT, MT, 8, false, false>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 1: MpkNode<VT, MT, 1, true, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 2: MpkNode<VT, MT, 2, true, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 4: MpkNode<VT, MT, 4, true, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        case 8: MpkNode<VT, MT, 8, true, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
+        default: MpkNode<VT, MT, 8, false, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
         }
     }
 };
 
+#ifndef MPK_BATCH_MIN_BLOCKS
+#define MPK_BATCH_MIN_BLOCKS 4
+#endif
+// Four CTAs per SM: the batch's items are short and latency-bound, so
+// resident warps matter more than the gathers in flight per lane.
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(kWaveThreads) k_batch_wave(BatchArgs b) {
+__global__ void __launch_bounds__(kWaveThreads, MPK_BATCH_MIN_BLOCKS) k_batch_wave(BatchArgs b) {
     __shared__ uint32_t s_epochs[kMaxBatch];
     for (int32_t m = threadIdx.x; m < b.count; m += blockDim.x)
         s_epochs[m] = (uint32_t)ld_relaxed_s32(b.plan_ctl[m] + CTL_EPOCH) + 1u;
