@@ -1152,7 +1152,7 @@ __global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
 // Gather budget of the batch's row kernel: 16-byte gathers of 16 values in
 // FP32; scalar gathers in FP64 (fits the batch kernel's register budget).
 template <typename VT>
-constexpr int batch_gather_budget() { return sizeof(VT) == 4 ? 16 : 0; }
+constexpr int kBatchGatherBudget = sizeof(VT) == 4 ? 16 : 0;
 
 template <typename VT, typename MT>
 struct BatchNode {
@@ -1164,7 +1164,7 @@ struct BatchNode {
     template <bool STAGED>
     __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &mv, int32_t t, int32_t k,
                                                int warp, int nwarps, int lane, const int &x) {
-        constexpr int GB = batch_gather_budget<VT>();
+        constexpr int GB = kBatchGatherBudget<VT>;
         switch (a.nrhs) {
         case 1: MpkNode<VT, MT, 1, true, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
         case 2: MpkNode<VT, MT, 2, true, false, GB>::template run<STAGED>(a, mv, t, k, warp, nwarps, lane, x); break;
