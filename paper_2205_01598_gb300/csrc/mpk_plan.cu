@@ -1070,7 +1070,10 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
     for (int32_t t = 0; t < T; t++) need = std::max(need, v[hi[t]] - v[t]);
     if (lag < 0) {   // in-flight items measured in level groups per power front
         const double tiles_per_group = (double)T / G;
-        lag = 1.5 * (double)pl->grid_ctas / ((double)p * tiles_per_group);
+        // the order is shared by the MPK and the Chebyshev launches: size the
+        // lag for the smaller of their grids
+        const int32_t grid = pl->cheb_grid > 0 ? std::min(pl->grid_ctas, pl->cheb_grid) : pl->grid_ctas;
+        lag = 1.5 * (double)grid / ((double)p * tiles_per_group);
     }
     const double sigma = std::max(1.0, need + lag);
     struct Item { double key; int32_t k, t; };
