@@ -539,14 +539,20 @@ struct MpkNode {
         VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
         VT acc[PC][1];
         slice_sum<VT, MT, 1, PC>(a, s, yin, lane, acc);
+        if (DIAG) {   // the diagonal terms' loads before any store (see row_out of ChebNode)
+            VT dv[PC], xv[PC];
 #pragma unroll
-        for (int i = 0; i < PC; i++) {
-            const int32_t r = s.row[i];
-            if (r < 0) continue;
-            VT v = acc[i][0];
-            if (DIAG) v = fma((VT)__ldg(a.diag + r), yin[r], v);
-            yout[r] = v;
+            for (int i = 0; i < PC; i++) {
+                const int32_t r = s.row[i];
+                dv[i] = r >= 0 ? (VT)__ldg(a.diag + r) : VT(0);
+                xv[i] = r >= 0 ? yin[r] : VT(0);
+            }
+#pragma unroll
+            for (int i = 0; i < PC; i++) acc[i][0] = fma(dv[i], xv[i], acc[i][0]);
         }
+#pragma unroll
+        for (int i = 0; i < PC; i++)
+            if (s.row[i] >= 0) yout[s.row[i]] = acc[i][0];
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
         for (int32_t c = s.c0 + warp + PC * nwarps; c < s.c1; c += nwarps)
             chunk_rows<VT, MT, 1, true, DIAG, false>(a, mv, c, lane, yin, yout);
@@ -1053,16 +1059,24 @@ struct ChebNode {
     // stored diagonal.
     __device__ __forceinline__ static void row_out(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
                                                    const VT (&s)[G]) {
-        double nv[G];
+        // every load before the first store: the ring blocks may alias as far
+        // as the compiler knows, and a load behind a store waits for it
+        double u[G], pv[G], nv[G];
         const double d = DIAG ? (double)__ldg(a.diag + r) : 0.0;
 #pragma unroll
         for (int q = 0; q < G; q++) {
-            const double u = (double)v.yin[G * (int64_t)r + q];
-            // the diagonal term enters in FP64 together with the shift
-            const double ah = DIAG ? ca.alpha * ((double)s[q] + d * u) + ca.beta * u : ca.alpha * (double)s[q] + ca.beta * u;
-            nv[q] = v.k > 1 ? 2.0 * ah - (double)v.yprev[G * (int64_t)r + q] : ah;
-            v.yout[G * (int64_t)r + q] = (VT)nv[q];
+            u[q] = (double)v.yin[G * (int64_t)r + q];
+            pv[q] = v.k > 1 ? (double)v.yprev[G * (int64_t)r + q] : 0.0;
         }
+#pragma unroll
+        for (int q = 0; q < G; q++) {
+            // the diagonal term enters in FP64 together with the shift
+            const double ah = DIAG ? ca.alpha * ((double)s[q] + d * u[q]) + ca.beta * u[q]
+                                   : ca.alpha * (double)s[q] + ca.beta * u[q];
+            nv[q] = v.k > 1 ? 2.0 * ah - pv[q] : ah;
+        }
+#pragma unroll
+        for (int q = 0; q < G; q++) v.yout[G * (int64_t)r + q] = (VT)nv[q];
         double *acc = ca.acc + G * (int64_t)r;
         if (G == 2) {
             acc[0] += v.cre * nv[0] - v.cim * nv[G - 1];
