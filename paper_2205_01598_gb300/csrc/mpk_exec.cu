@@ -1057,8 +1057,38 @@ struct ChebNode {
 
     // Row r of the sweep step, given s = (A v_{k-1})[r] without a separately
     // stored diagonal.
+    // complex state, written out for two columns (this form schedules better
+    // than the loop over columns below)
+    __device__ __forceinline__ static void row_out2(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
+                                                    VT s0, VT s1) {
+        const double u0 = (double)v.yin[2 * (int64_t)r], u1 = (double)v.yin[2 * (int64_t)r + 1];
+        double a0, a1;
+        if (DIAG) {   // the diagonal term enters in FP64 together with the shift
+            const double d = (double)__ldg(a.diag + r);
+            a0 = ca.alpha * ((double)s0 + d * u0) + ca.beta * u0;
+            a1 = ca.alpha * ((double)s1 + d * u1) + ca.beta * u1;
+        } else {
+            a0 = ca.alpha * (double)s0 + ca.beta * u0;
+            a1 = ca.alpha * (double)s1 + ca.beta * u1;
+        }
+        double n0 = a0, n1 = a1;
+        if (v.k > 1) {
+            n0 = 2.0 * a0 - (double)v.yprev[2 * (int64_t)r];
+            n1 = 2.0 * a1 - (double)v.yprev[2 * (int64_t)r + 1];
+        }
+        v.yout[2 * (int64_t)r] = (VT)n0;
+        v.yout[2 * (int64_t)r + 1] = (VT)n1;
+        double *acc = ca.acc + 2 * (int64_t)r;
+        acc[0] += v.cre * n0 - v.cim * n1;
+        acc[1] += v.cre * n1 + v.cim * n0;
+    }
+
     __device__ __forceinline__ static void row_out(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
                                                    const VT (&s)[G]) {
+        if constexpr (G == 2) {
+            row_out2(a, ca, v, r, s[0], s[G - 1]);
+            return;
+        }
         // every load before the first store: the ring blocks may alias as far
         // as the compiler knows, and a load behind a store waits for it
         double u[G], pv[G], nv[G];
@@ -1096,6 +1126,29 @@ struct ChebNode {
         const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
         const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
         const int64_t e0 = off + lane;
+        if constexpr (G == 2) {   // complex state: two scalar sums
+            VT s0 = VT(0), s1 = VT(0);
+            constexpr int B = 8;
+            for (int32_t q0 = 0; q0 < w; q0 += B) {
+                int32_t cols[B];
+                VT vals[B];
+#pragma unroll
+                for (int u = 0; u < B; u++) {
+                    const bool in = q0 + u < w;
+                    cols[u] = in ? mv.c(e0 + (int64_t)(q0 + u) * kChunk) : -1;
+                    vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(q0 + u) * kChunk)) : VT(0);
+                }
+#pragma unroll
+                for (int u = 0; u < B; u++) {
+                    if (cols[u] >= 0) {
+                        s0 = fma(vals[u], v.yin[2 * (int64_t)cols[u]], s0);
+                        s1 = fma(vals[u], v.yin[2 * (int64_t)cols[u] + 1], s1);
+                    }
+                }
+            }
+            row_out2(a, ca, v, r, s0, s1);
+            return;
+        }
         VT sum[G];
 #pragma unroll
         for (int q = 0; q < G; q++) sum[q] = VT(0);
@@ -1141,8 +1194,11 @@ struct ChebNode {
         VT acc[PC][G];
         slice_sum<VT, MT, G, PC>(a, s, v.yin, lane, acc);
 #pragma unroll
-        for (int i = 0; i < PC; i++)
-            if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i]);
+        for (int i = 0; i < PC; i++) {
+            if (s.row[i] < 0) continue;
+            if constexpr (G == 2) row_out2(a, ca, v, s.row[i], acc[i][0], acc[i][G - 1]);
+            else row_out(a, ca, v, s.row[i], acc[i]);
+        }
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
         for (int32_t c = s.c0 + warp + PC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
     }
