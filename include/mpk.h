@@ -88,7 +88,8 @@ typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
 
 /* A square sparse matrix in CRS form (Sec. 3.1, Fig. 1).  Device pointers,
  * caller-owned.  rowptr[n+1] (rowptr[0] = 0, non-decreasing, rowptr[n] = nnz),
- * col[nnz] in [0, n), val[nnz] FP64.  Column order inside a row is free.
+ * col[nnz] in [0, n), val[nnz] FP64 (col and val may be NULL when nnz = 0).
+ * Column order inside a row is free.
  * assume_symmetric != 0 promises a structurally symmetric pattern; with 0 the
  * levels are computed on the pattern of A + A^T (Sec. 4 restricts the method
  * to symmetric patterns; the MPK itself always multiplies by A).          */
@@ -156,7 +157,8 @@ int mpk_opts_default(mpk_opts *o);
  * entry of the chosen precision), the packed SELL-32 matrix (rows of a work
  * item sorted by length when that cuts the padding by more than 10%) and the
  * dependency ranges of the wavefront.  1 <= p <= 255, 1 <= nrhs <= 64.
- * Errors: MPK_ERR_INVALID (NULL pointers, n < 1, p or nrhs out of range,
+ * Errors: MPK_ERR_INVALID (NULL rowptr, or NULL col / val with nnz > 0,
+ * n < 1, p or nrhs out of range,
  * malformed CRS found on the device), MPK_ERR_OOM, MPK_ERR_CUDA.  On error
  * *out is set to NULL and nothing is leaked.                              */
 int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out);

@@ -1124,7 +1124,8 @@ int mpk_opts_default(mpk_opts *o) {
 int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out) {
     if (!out) return MPK_ERR_INVALID;
     *out = nullptr;
-    if (!A || !o || !A->rowptr || !A->col || !A->val) return MPK_ERR_INVALID;
+    if (!A || !o || !A->rowptr) return MPK_ERR_INVALID;
+    if (A->nnz > 0 && (!A->col || !A->val)) return MPK_ERR_INVALID;   // unused when there are no entries
     if (A->n < 1 || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return MPK_ERR_INVALID;
     if (p < 1 || p > kMaxP) return MPK_ERR_INVALID;
     if (o->nrhs < 1 || o->nrhs > kMaxNrhs) return MPK_ERR_INVALID;
@@ -1217,7 +1218,8 @@ const char *mpk_strerror(int status) {
 
 int mpk_levels_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, int32_t root,
                        int32_t *level, int32_t *n_levels, void *stream, double timeout_s) {
-    if (!rowptr || !col || !level || !n_levels || n < 1 || nnz < 0 || nnz >= (int64_t)INT32_MAX) return MPK_ERR_INVALID;
+    if (!rowptr || (nnz > 0 && !col) || !level || !n_levels || n < 1 || nnz < 0 || nnz >= (int64_t)INT32_MAX)
+        return MPK_ERR_INVALID;
     if (root < 0 || root >= n) return MPK_ERR_INVALID;
     if (n > kStaticLevelsMaxN) return MPK_ERR_UNSUPPORTED;   // beyond the static scratch
     cudaStream_t st = (cudaStream_t)stream;
