@@ -90,3 +90,28 @@ def test_one_power_per_launch_is_bitwise_equal(prec):
     mpk.mpk_cheb(plan, coef, c, r, xd, y1)
     mpk.mpk_cheb(plan, coef, c, r, xd, y2, one_power_per_launch=True)
     assert torch.equal(y1, y2)
+
+
+def test_anderson_200_full_size_bf16():
+    """The 200^3 Anderson workload (N = 8M, nnz = 56M), degree 64 in sweeps of
+    p = 8, BF16 hoppings, in the benchmark's launch configuration (level
+    order): error against the FP64 oracle on every output within the
+    reduced-precision bound."""
+    A = mi.anderson3d(200, W=16.5, seed=42)
+    assert A.nnz == 56_000_000
+    plan = plan_of(A, 8, prec="bf16val", nrhs=2)
+    assert mpk.mpk_plan_info(plan)["val_bytes"] == 2
+    lo, hi = mpk.mpk_gershgorin(plan)
+    c, r = (hi + lo) / 2, (hi - lo) / 2
+    coef = mpk.mpk_cheb_coeffs_schroedinger(64, c, r, 50.0 / r)
+    psi = mi.uniform(1234, A.n) + 1j * mi.uniform(4321, A.n)
+    psi /= np.linalg.norm(psi)
+    ref = oracle.cheb(A, coef, c, r, psi)
+    perm = mpk.mpk_plan_perm(plan)[0].cpu().numpy()
+    x = np.stack([psi.real, psi.imag], 1)[perm]
+    xd = torch.from_numpy(np.ascontiguousarray(x)).float().cuda()
+    yd = torch.empty(A.n, 2, dtype=torch.float64, device="cuda")
+    mpk.mpk_cheb(plan, coef, c, r, xd, yd, permuted=True)
+    y = yd.cpu().numpy()
+    got = y[:, 0] + 1j * y[:, 1]
+    assert np.max(np.abs(got - ref[perm])) / np.max(np.abs(ref)) <= 2e-5

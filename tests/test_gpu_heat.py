@@ -92,3 +92,22 @@ def test_heat_rejects_complex_plan():
     with pytest.raises(mpk.MpkError) as e:
         mpk.mpk_cheb_real(plan, np.ones(5), 0.0, 1.0, x, y)
     assert e.value.code == mpk.MPK_ERR_INVALID
+
+
+def test_heat_order4_160_full_size():
+    """The order-4 160^3 heat workload (nnz = 52,787,200, Tab. 3), degree 64
+    in sweeps of 8, FP64, level order as the benchmark runs it."""
+    A = mi.star3d(160, 2)
+    assert A.nnz == 52_787_200
+    plan = plan_of(A, 8, prec="f64", nrhs=1)
+    lo, hi = mpk.mpk_gershgorin(plan)
+    lo = max(lo, 0.0)
+    c, r = (hi + lo) / 2, (hi - lo) / 2
+    coef = mpk.mpk_cheb_coeffs_heat(64, c, r, 50.0 / r)
+    x = mi.random_vector(A.n, 1234)
+    ref = oracle.cheb_real(A, coef, c, r, x)
+    perm = mpk.mpk_plan_perm(plan)[0].cpu().numpy()
+    xd = torch.from_numpy(np.ascontiguousarray(x[perm])).cuda()
+    yd = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    mpk.mpk_cheb_real(plan, coef, c, r, xd, yd, permuted=True)
+    assert np.max(np.abs(yd.cpu().numpy() - ref[perm])) / np.max(np.abs(x)) <= 1e-12
