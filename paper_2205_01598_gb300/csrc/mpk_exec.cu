@@ -1350,9 +1350,10 @@ const void *spmv_ptr(int nrhs) {
 template <bool STAGED>
 const void *pick_wave_t(const Plan *pl) {
     if (pl->prec == MPK_F64) return wave_ptr<double, double, false, STAGED, STAGED ? kComputeWarps : kFp64Warps>(pl->nrhs);
-    if (!pl->has_diag) return wave_ptr<float, float, false, STAGED>(pl->nrhs);
-    if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, STAGED>(pl->nrhs);
-    return wave_ptr<float, float, true, STAGED>(pl->nrhs);
+    constexpr int NW = STAGED ? kComputeWarps : kFp32Warps;
+    if (!pl->has_diag) return wave_ptr<float, float, false, STAGED, NW>(pl->nrhs);
+    if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, STAGED, NW>(pl->nrhs);
+    return wave_ptr<float, float, true, STAGED, NW>(pl->nrhs);
 }
 template <bool STAGED, int G>
 const void *pick_cheb_g(const Plan *pl) {

@@ -21,6 +21,10 @@ constexpr int kMaxNrhs = 64;
 #endif
 constexpr int kComputeWarps = MPK_COMPUTE_WARPS;         // warps that compute work items
 constexpr int kFp64Warps = 16;                           // compute warps of the FP64 MPK wavefront
+#ifndef MPK_F32_WARPS
+#define MPK_F32_WARPS MPK_COMPUTE_WARPS
+#endif
+constexpr int kFp32Warps = MPK_F32_WARPS;                // compute warps of the FP32 / BF16 MPK wavefront
 constexpr int kWaveThreads = (kComputeWarps + 1) * 32;   // plus one scheduler warp
 constexpr int kSpmvThreads = 256;                        // baseline SpMV CTA
 #ifndef MPK_RES_WARPS

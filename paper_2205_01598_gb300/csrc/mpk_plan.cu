@@ -944,7 +944,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
             pl->smem_bytes = pl->staged ? need : 0;
         }
-        pl->wave_warps = (pl->prec == MPK_F64 && !pl->staged && !pl->resident) ? kFp64Warps : kComputeWarps;
+        pl->wave_warps = pl->staged || pl->resident ? kComputeWarps : (pl->prec == MPK_F64 ? kFp64Warps : kFp32Warps);
     }
 
     // 11. grid size, then the work list: a skewed diagonal order of the Lp
@@ -968,7 +968,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         } else {
             pl->resident = 0;
             pl->smem_bytes = 0;
-            pl->wave_warps = pl->prec == MPK_F64 ? kFp64Warps : kComputeWarps;
+            pl->wave_warps = pl->prec == MPK_F64 ? kFp64Warps : kFp32Warps;
         }
     }
     if (!pl->resident) {
