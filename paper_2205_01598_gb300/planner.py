@@ -9,7 +9,7 @@ candidate, log(t_c / t_best); the planner picks the argmin.  The network is
 trained on the GPU with the library's own kernels (mpk_mlp_*) on timings the
 autotuner (mpk_autotune) measured on generated matrices.  The autotuner is
 the fallback (no weights, or a predicted configuration that fails) and the
-judge of regret, regret = t(chosen) / t(best) - 1.
+yardstick of regret, regret = t(chosen) / t(best) - 1.
 
 Command line (GPU):
   python -m paper_2205_01598_gb300.planner collect --first 7000 --count 300 --out data.npz
