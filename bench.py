@@ -185,17 +185,37 @@ def time_oracle(A, x, p, budget_s=12.0):
     return 2.0 * A.nnz * p * reps / el / 1e9, reps, el
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """Replicas under torchrun: one process per GPU (RANK / LOCAL_RANK /
+    WORLD_SIZE / MASTER_* from the environment), no data-path collective;
+    the group only carries the barrier and the max-over-ranks timing."""
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
         return rank, ws, dist
     return 0, 1, None
+
+
+def max_over_ranks(ms, dist, device="cuda"):
+    """The slowest rank's time: the whole job is done when every replica is."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(work_per_rank, world_size, ms):
+    """Throughput of the whole job: every rank did work_per_rank units
+    (weak scaling) in ms milliseconds; in units per second / 1e9."""
+    return world_size * work_per_rank / (ms * 1e-3) / 1e9
 
 
 def main():
@@ -276,18 +296,13 @@ def main():
             total = sum(b.elapsed_time(e) for b, e in evs)
         if dist:
             dist.barrier()
-        ms = total / steps
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(total / steps, dist)
 
     # headline: level-blocked MPK, one persistent launch per step
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     ms = timed(lambda: mpk.mpk_run(plan, x, Y, permuted=True, asynchronous=True), args.steps, args.warmup, sampler)
     mpk.mpk_run(plan, x, Y, permuted=True)   # synchronous call: surfaces any device-side error
-    value = ws * flops / (ms * 1e-3) / 1e9
+    value = whole_job_value(flops, ws, ms)
 
     # baseline: p back-to-back SpMVs over the same packed matrix, same GPU
     ms_base = timed(lambda: mpk.mpk_baseline_run(plan, x, Y, permuted=True, asynchronous=True),
@@ -305,7 +320,7 @@ def main():
         Yh.copy_(Y, non_blocking=True)
 
     ms_e2e = timed(e2e_step, max(3, min(args.steps, 20)), 2)
-    value_e2e = ws * flops / (ms_e2e * 1e-3) / 1e9
+    value_e2e = whole_job_value(flops, ws, ms_e2e)
 
     peaks, peak_src = load_peaks()
     traffic = recorded_traffic("k_wave_laplace3d160_p8.md", prec) if (kind, size, p) == ("laplace3d", 160, 8) else None
@@ -357,7 +372,7 @@ def main():
         "data": "synthetic",
         "config": cfg,
         "speedup_vs_pxspmv": round(ms_base / ms, 4),
-        "baseline_pxspmv": {"ms_per_step": round(ms_base, 5), "value": round(ws * flops / (ms_base * 1e-3) / 1e9, 3),
+        "baseline_pxspmv": {"ms_per_step": round(ms_base, 5), "value": round(whole_job_value(flops, ws, ms_base), 3),
                             "gpu_launches_per_step": p},
         "e2e": {"value": round(value_e2e, 3), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": A.n * x.element_size(),
@@ -520,6 +535,9 @@ def run_cheb(args, kind, size, p, prec, cfg):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ctx = sampler if sampler is not None else _Null()
         with ctx:
@@ -528,7 +546,9 @@ def run_cheb(args, kind, size, p, prec, cfg):
                 fn()
             e1.record(st)
             torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        if dist:
+            dist.barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / steps, dist)
 
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     ms = timed(lambda: run(plan, coef, c, r, x, y, permuted=True, asynchronous=True), args.steps, args.warmup, sampler)
@@ -576,13 +596,13 @@ def run_cheb(args, kind, size, p, prec, cfg):
         cpu = {"value": round(flops / el / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"one full Chebyshev step (M={CHEB_M}) in {el:.1f} s (sequential FP64 C)"}
     out = {
-        "metric": "Chebyshev propagation SpMV GFLOP/s (2*nnz*cols*M/t)", "value": round(flops / (ms * 1e-3) / 1e9, 3),
+        "metric": "Chebyshev propagation SpMV GFLOP/s (2*nnz*cols*M/t)", "value": round(whole_job_value(flops, ws, ms), 3),
         "unit": "GFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"f64": "f64"}.get(prec, "f32"),
         "data": "synthetic", "config": cfg, "error_vs_fp64_oracle": err,
         "speedup_vs_one_power_per_launch": round(ms_base / ms, 4),
         "baseline_one_power_per_launch": {"ms_per_step": round(ms_base, 4), "gpu_launches_per_step": CHEB_M},
-        "e2e": {"value": round(flops / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+        "e2e": {"value": round(whole_job_value(flops, ws, ms_e2e), 3), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(np.prod(x.shape)) * xd.element_size(),
                 "d2h_bytes_per_step": int(np.prod(y.shape)) * 8, "ms_per_step": round(ms_e2e, 4)},
         "gpu_launches": args.steps * (-(-CHEB_M // p) + 1), "roofline": roof, "cpu_baseline": cpu,
