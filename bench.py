@@ -612,6 +612,8 @@ def run_cheb(args, kind, size, p, prec, cfg):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 class _Null:
