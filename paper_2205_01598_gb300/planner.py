@@ -193,21 +193,24 @@ def evaluate(planner, F, MS):
             "within_10pct_mlp": float(np.mean(r_mlp <= 0.10)), "within_10pct_default": float(np.mean(r_def <= 0.10))}
 
 
-def plan_options(rowptr, col, val, prec="f32", planner=None):
+def plan_options(rowptr, col, val, prec="f32", planner=None, use_weights=True):
     """Options for the MPK of a matrix: the network's choice, or the
     autotuner's when there is no network or the choice fails to plan."""
     g = grid()
-    if planner is None and os.path.exists(WEIGHTS):
+    if planner is None and use_weights and os.path.exists(WEIGHTS):
         planner = Planner.load()
     if planner is not None:
         probe = mpk_plan(rowptr, col, val, K_POWERS, prec=prec)
-        c = g[int(planner.choose(mpk_plan_features(probe))[0])]
+        i = int(planner.choose(mpk_plan_features(probe))[0])
         del probe
-        try:
-            mpk_plan(rowptr, col, val, c["p_sweep"], prec=prec, tile_rows=c["tile_rows"], safety_f=c["safety_f"])
-            return dict(c, source="mlp")
-        except RuntimeError:
-            pass
+        if 0 <= i < len(g):
+            c = g[i]
+            try:
+                mpk_plan(rowptr, col, val, c["p_sweep"], prec=prec, tile_rows=c["tile_rows"],
+                         safety_f=c["safety_f"], tune=c.get("tune", 0))
+                return dict(c, source="mlp")
+            except RuntimeError:
+                pass
     best, _ = mpk_autotune(rowptr, col, val, K_POWERS, g, prec=prec)
     return dict(g[best], source="autotuner")
 

@@ -106,3 +106,23 @@ def test_planner_beats_default(lib):
     r_def = P.regret(MS, np.zeros(len(MS), dtype=int))
     assert r_mlp.mean() <= r_def.mean(), (r_mlp, r_def)
     assert r_mlp.mean() <= 0.10, r_mlp   # within 10 % of the autotuner's best on average
+
+
+def test_plan_options_network_and_fallbacks(lib):
+    """plan_options: the network's pick when weights ship; the full
+    autotuner without weights, or when the network names no grid entry."""
+    from paper_2205_01598_gb300 import csr_to_device
+    from paper_2205_01598_gb300 import planner as P
+    A = mi.laplace3d(30)
+    rp, cl, va = csr_to_device(A)
+    g = P.grid()
+    if os.path.exists(P.WEIGHTS):
+        opt = P.plan_options(rp, cl, va)
+        assert opt["source"] == "mlp" and {k: opt[k] for k in g[0]} in g
+    opt = P.plan_options(rp, cl, va, use_weights=False)
+    assert opt["source"] == "autotuner" and {k: opt[k] for k in g[0]} in g
+
+    class Broken:
+        def choose(self, feats):
+            return np.array([len(g) + 5])
+    assert P.plan_options(rp, cl, va, planner=Broken())["source"] == "autotuner"
