@@ -183,6 +183,14 @@ int mpk_plan_features(mpk_plan_t plan, float *out, int32_t count);
 int mpk_plan_perm(mpk_plan_t plan, int32_t *perm, int32_t *level_ptr, int32_t *group_ptr,
                   int32_t *level);
 
+/* The plan's schedule, copied to HOST arrays: work[n_tiles * p] = the issue
+ * order of the work items, item = (tile << 8) | power; dep_lo / dep_hi
+ * [n_tiles] = the range of tiles whose power k-1 a tile's power k waits for
+ * (conditions (A)-(C) of Sec. 4.3 at tile granularity).  Every dependency of
+ * an item precedes it in the order, which the in-order dealing of the
+ * persistent launch relies on.  MPK_ERR_INVALID on NULL arguments.          */
+int mpk_plan_schedule(mpk_plan_t plan, int32_t *work, int32_t *dep_lo, int32_t *dep_hi);
+
 /* Level-blocked MPK (Sec. 4, Fig. 5 with level groups and point-to-point
  * synchronisation): Y[k-1] = A^k x for k = 1..p in ONE persistent launch.
  * x: n x nrhs row-major; Y: p consecutive blocks of n x nrhs.  Element type

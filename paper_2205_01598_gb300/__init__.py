@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
-SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu"]
+SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -117,6 +117,7 @@ def load(path: str | None = None):
             "mpk_plan": ([C.POINTER(mpk_csr), i32, C.POINTER(mpk_opts), C.POINTER(vp)], C.c_int),
             "mpk_plan_info": ([vp, C.POINTER(mpk_plan_stats)], C.c_int),
             "mpk_plan_perm": ([vp, vp, vp, vp, vp], C.c_int),
+            "mpk_plan_schedule": ([vp, vp, vp, vp], C.c_int),
             "mpk_run": ([vp, vp, vp, u32], C.c_int),
             "mpk_baseline_run": ([vp, vp, vp, u32], C.c_int),
             "mpk_gershgorin": ([vp, C.POINTER(f64), C.POINTER(f64)], C.c_int),
@@ -288,6 +289,17 @@ def mpk_plan_perm(plan: Plan):
     lev = torch.empty(plan.n, dtype=torch.int32, device=dev)
     _check(load().mpk_plan_perm(plan.handle, _ptr(perm), _ptr(lp), _ptr(gp), _ptr(lev)), "mpk_plan_perm")
     return perm, lp, gp, lev
+
+
+def mpk_plan_schedule(plan: Plan):
+    """(work, dep_lo, dep_hi) as host int32 arrays (mpk_plan_schedule)."""
+    info = mpk_plan_info(plan)
+    work = np.empty(info["n_tiles"] * plan.p, dtype=np.int32)
+    lo = np.empty(info["n_tiles"], dtype=np.int32)
+    hi = np.empty(info["n_tiles"], dtype=np.int32)
+    _check(load().mpk_plan_schedule(plan.handle, work.ctypes.data_as(C.c_void_p), lo.ctypes.data_as(C.c_void_p),
+                                    hi.ctypes.data_as(C.c_void_p)), "mpk_plan_schedule")
+    return work, lo, hi
 
 
 def _flags(permuted, asynchronous):
