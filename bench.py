@@ -411,6 +411,8 @@ def run_batch(args):
         n = n_lo + int(z[0] % np.uint64(n_hi - n_lo + 1))
         specs.append((m, 1000 + m, n, 1 + int(z[1] % np.uint64(16)), 2 + int(z[2] % np.uint64(9))))
     # matrices are generated on the host cores before the first CUDA call (spawned workers)
+    if args.impl == "reference":
+        return run_batch_reference(args, specs, desc, count)
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         mats = dict(pool.map(_gen_batch_member, [(m, seed, n) for m, seed, n, _, _ in specs]))
@@ -624,9 +626,23 @@ class _Null:
         return False
 
 
+def _reference_line(args, metric, work, el, steps, warm, cfg, sample):
+    value = work / el / 1e9
+    return {"impl": "reference", "metric": metric, "value": round(value, 4), "unit": "GFLOP/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": warm,
+            "ms_per_step": round(el / steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def run_reference(args, kind, size, p, cfg):
     """Reference arm: the FP64 CPU oracle (sequential C) on the host cores,
-    rank 0 only; each step is one full MPK of the workload."""
+    rank 0 only; W untimed warm-up steps, then exactly K timed steps, each a
+    bounded sample of the workload: one full MPK (MPK configs) or one sweep
+    of 8 Chebyshev steps (the first 8 terms of the expansion; Chebyshev
+    configs)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -635,42 +651,74 @@ def run_reference(args, kind, size, p, cfg):
     oracle.build()
     A = make_matrix(kind, size)
     cfg["n"], cfg["nnz"] = A.n, A.nnz
-    if kind in ("anderson3d", "heat"):   # Chebyshev configs: one propagation step per step
+    if kind in ("anderson3d", "heat"):
         lo, hi = oracle.gershgorin(A)
         if kind == "heat":   # -Delta is positive semi-definite: spectrum in [0, hi]
             lo = max(lo, 0.0)
         c, r = (hi + lo) / 2, (hi - lo) / 2
-        cols = 1 if kind == "heat" else 2
+        cols, terms = (1 if kind == "heat" else 2), p
         if kind == "heat":
-            coef = oracle.cheb_coeffs_heat(CHEB_M, c, r, CHEB_RDT / r)
+            coef = oracle.cheb_coeffs_heat(CHEB_M, c, r, CHEB_RDT / r)[:terms + 1]
             x = mi.random_vector(A.n, 1234)
             step = lambda: oracle.cheb_real(A, coef, c, r, x)   # noqa: E731
         else:
-            coef = oracle.cheb_coeffs_schroedinger(CHEB_M, c, r, CHEB_RDT / r)
+            coef = oracle.cheb_coeffs_schroedinger(CHEB_M, c, r, CHEB_RDT / r)[:terms + 1]
             x = mi.uniform(1234, A.n) + 1j * mi.uniform(4321, A.n)
             step = lambda: oracle.cheb(A, coef, c, r, x)   # noqa: E731
-        work, metric, sample = 2.0 * A.nnz * cols * CHEB_M, "Chebyshev propagation SpMV GFLOP/s (2*nnz*cols*M/t)", \
-            f"full Chebyshev steps (M={CHEB_M}) of the workload"
-        steps, warm = max(1, min(args.steps, 5)), 0
+        work = 2.0 * A.nnz * cols * terms
+        metric = "Chebyshev propagation SpMV GFLOP/s (2*nnz*cols*M/t)"
+        sample = f"one sweep of {terms} Chebyshev steps (of M={CHEB_M}) of the full workload per step"
     else:
         x = mi.random_vector(A.n, 1234)
         step = lambda: oracle.mpk(A, x, p)   # noqa: E731
-        work, metric, sample = 2.0 * A.nnz * p, "MPK GFLOP/s (2*nnz*p/t)", f"full MPK runs (p={p}) of the workload"
-        steps, warm = max(1, min(args.steps, 10)), max(0, min(args.warmup, 1))
+        work, metric = 2.0 * A.nnz * p, "MPK GFLOP/s (2*nnz*p/t)"
+        sample = f"one full MPK (p={p}) of the workload per step"
+    steps, warm = max(1, args.steps), max(0, args.warmup)
     for _ in range(warm):
         step()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     el = time.perf_counter() - t0
-    value = work * steps / el / 1e9
-    out = {"impl": "reference", "metric": metric, "value": round(value, 4), "unit": "GFLOP/s",
-           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": warm,
-           "ms_per_step": round(el / steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-           "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                            "sample": f"{steps} {sample}"},
-           "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    out = _reference_line(args, metric, work * steps, el, steps, warm, cfg,
+                          f"{steps} timed steps after {warm} warm-up; {sample} (sequential FP64 C)")
+    print(json.dumps(out), flush=True)
+
+
+def run_batch_reference(args, specs, desc, count):
+    """Reference arm of the batched workload: the FP64 CPU oracle, rank 0
+    only; step i is the MPK of batch member i mod count (its own nrhs and p),
+    W untimed warm-up steps, then exactly K timed steps."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    import oracle
+    import mpk_inputs as mi
+    oracle.build()
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    used = sorted({i % count for i in range(warm + steps)})
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        mats = dict(pool.map(_gen_batch_member, [(specs[m][0], specs[m][1], specs[m][2]) for m in used]))
+    xs = {m: np.stack([mi.random_vector(mats[m].n, 2000 + 17 * m + q) for q in range(specs[m][3])], axis=1)
+          for m in used}
+
+    def step(i):
+        m = i % count
+        oracle.mpk(mats[m], xs[m], specs[m][4])
+        return 2.0 * mats[m].nnz * specs[m][3] * specs[m][4]
+
+    for i in range(warm):
+        step(i)
+    work = 0.0
+    t0 = time.perf_counter()
+    for i in range(warm, warm + steps):
+        work += step(i)
+    el = time.perf_counter() - t0
+    cfg = {"workload": desc, "matrices": count, "data": "synthetic"}
+    out = _reference_line(args, "batched MPK GFLOP/s (sum 2*nnz*nrhs*p / t)", work, el, steps, warm, cfg,
+                          f"{steps} timed steps after {warm} warm-up; step i = the MPK of batch member i mod "
+                          f"{count} with its nrhs and p (sequential FP64 C)")
     print(json.dumps(out), flush=True)
 
 

@@ -51,3 +51,23 @@ def test_reference_arm_idles_outside_rank_zero(monkeypatch, capsys):
     args = type("A", (), {"steps": 1, "warmup": 0})()
     assert bench.run_reference(args, "laplace2d", 64, 4, {}) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_times_exactly_k_steps(monkeypatch, capsys):
+    """Rank 0 runs W untimed warm-up steps and exactly K timed ones, and
+    prints one JSON line with the keys the reference arm carries."""
+    import json
+    import bench
+    import oracle
+    calls = []
+    real = oracle.mpk
+    monkeypatch.setattr(oracle, "mpk", lambda A, x, p: calls.append(p) or real(A, x, p))
+    monkeypatch.setenv("RANK", "0")
+    args = type("A", (), {"steps": 4, "warmup": 3})()
+    bench.run_reference(args, "laplace2d", 64, 4, {"workload": "2D 64^2"})
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert calls == [4] * 7
+    assert line["impl"] == "reference" and line["steps"] == 4 and line["warmup"] == 3
+    assert line["config"]["nnz"] == 20224 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
