@@ -179,6 +179,37 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _want(t, numel, dtype, name):
+    """Checks a tensor that an entry point reads or writes as `numel`
+    elements of `dtype`: the C ABI cannot see sizes, so a mismatch is
+    rejected here, before anything is launched."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+
+
+def _ptrs(*specs):
+    """Device pointers of (tensor, numel, dtype, name) specs, all checked first."""
+    for spec in specs:
+        _want(*spec)
+    return [_ptr(spec[0]) for spec in specs]
+
+
+def _csr(rowptr, col, val, assume_symmetric):
+    import torch
+    for t, dt, name in ((rowptr, torch.int32, "rowptr"), (col, torch.int32, "col"), (val, torch.float64, "val")):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt:
+            raise TypeError(f"{name}: expected a {dt} tensor")
+    if rowptr.numel() < 1 or col.numel() != val.numel():
+        raise ValueError("rowptr needs n + 1 entries and col / val the same length nnz")
+    return mpk_csr(n=rowptr.numel() - 1, nnz=col.numel(), rowptr=_ptr(rowptr), col=_ptr(col), val=_ptr(val),
+                   assume_symmetric=int(bool(assume_symmetric)))
+
+
 def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -215,11 +246,8 @@ def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=
              stream=None) -> Plan:
     """Level-blocked plan of the CRS matrix (rowptr, col: int32 CUDA tensors,
     val: float64 CUDA tensor) for powers 1..p (mpk_plan)."""
-    import torch
+    A = _csr(rowptr, col, val, assume_symmetric)
     lib = load()
-    assert rowptr.dtype == torch.int32 and col.dtype == torch.int32 and val.dtype == torch.float64
-    A = mpk_csr(n=rowptr.numel() - 1, nnz=col.numel(), rowptr=_ptr(rowptr), col=_ptr(col), val=_ptr(val),
-                assume_symmetric=int(bool(assume_symmetric)))
     o = mpk_opts_default()
     o.root, o.cache_bytes, o.safety_f = int(root), float(cache_bytes), float(safety_f)
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
@@ -246,9 +274,8 @@ def mpk_autotune(rowptr, col, val, k, candidates, *, prec="f64", nrhs=1, min_tim
     """Times each candidate (dicts with tile_rows, safety_f, tune, p_sweep) for
     the MPK with k powers (mpk_autotune); returns (best index, list of ms
     (-1 for failures))."""
+    A = _csr(rowptr, col, val, assume_symmetric)
     lib = load()
-    A = mpk_csr(n=rowptr.numel() - 1, nnz=col.numel(), rowptr=_ptr(rowptr), col=_ptr(col), val=_ptr(val),
-                assume_symmetric=int(bool(assume_symmetric)))
     o = mpk_opts_default()
     o.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     o.nrhs = int(nrhs)
@@ -306,15 +333,22 @@ def _flags(permuted, asynchronous):
     return (MPK_IO_PERMUTED if permuted else 0) | (MPK_ASYNC if asynchronous else 0)
 
 
+def _mpk_io(plan, x, Y):
+    blk = plan.n * plan.nrhs
+    return _ptrs((x, blk, plan.vec_dtype, "x"), (Y, plan.p * blk, plan.vec_dtype, "Y"))
+
+
 def mpk_run(plan: Plan, x, Y, permuted=False, asynchronous=False):
-    """Y[k-1] = A^k x, k = 1..p, level-blocked (mpk_run)."""
-    _check(load().mpk_run(plan.handle, _ptr(x), _ptr(Y), _flags(permuted, asynchronous)), "mpk_run")
+    """Y[k-1] = A^k x, k = 1..p, level-blocked (mpk_run); x: n x nrhs, Y:
+    p x n x nrhs, both in the plan's vector precision."""
+    xp, yp = _mpk_io(plan, x, Y)
+    _check(load().mpk_run(plan.handle, xp, yp, _flags(permuted, asynchronous)), "mpk_run")
 
 
 def mpk_baseline_run(plan: Plan, x, Y, permuted=False, asynchronous=False):
     """Y[k-1] = A^k x by p back-to-back SpMV launches (mpk_baseline_run)."""
-    _check(load().mpk_baseline_run(plan.handle, _ptr(x), _ptr(Y), _flags(permuted, asynchronous)),
-           "mpk_baseline_run")
+    xp, yp = _mpk_io(plan, x, Y)
+    _check(load().mpk_baseline_run(plan.handle, xp, yp, _flags(permuted, asynchronous)), "mpk_baseline_run")
 
 
 def mpk_gershgorin(plan: Plan):
@@ -342,9 +376,11 @@ def mpk_cheb_real(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=Fal
     """y = sum_k coef_k T_k((A - c)/r) x for real x (n,) in the plan precision
     and y (n,) float64 CUDA tensors; coef: real host array of length M+1
     (mpk_cheb_real)."""
+    import torch
     ci = np.ascontiguousarray(coef, dtype=np.float64)
+    xp, yp = _ptrs((x, plan.n * plan.nrhs, plan.vec_dtype, "x"), (y, plan.n * plan.nrhs, torch.float64, "y"))
     _check(load().mpk_cheb_real(plan.handle, ci.ctypes.data_as(C.c_void_p), ci.shape[0] - 1, float(c), float(r),
-                                _ptr(x), _ptr(y),
+                                xp, yp,
                                 _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)),
            "mpk_cheb_real")
 
@@ -352,17 +388,23 @@ def mpk_cheb_real(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=Fal
 def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False, one_power_per_launch=False):
     """y = sum_k coef_k T_k((A - c)/r) x (mpk_cheb); x: (n, 2) plan precision,
     y: (n, 2) float64 CUDA tensors; coef: complex host array of length M+1."""
+    import torch
     coef = np.asarray(coef, dtype=np.complex128)
     ci = np.empty(2 * coef.shape[0], dtype=np.float64)
     ci[0::2], ci[1::2] = coef.real, coef.imag
+    xp, yp = _ptrs((x, plan.n * plan.nrhs, plan.vec_dtype, "x"), (y, plan.n * plan.nrhs, torch.float64, "y"))
     _check(load().mpk_cheb(plan.handle, ci.ctypes.data_as(C.c_void_p), coef.shape[0] - 1, float(c), float(r),
-                           _ptr(x), _ptr(y),
+                           xp, yp,
                            _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)), "mpk_cheb")
 
 
 def mpk_permute_vectors(plan: Plan, src, dst, count, to_level):
-    _check(load().mpk_permute_vectors(plan.handle, _ptr(src), _ptr(dst), int(count), src.element_size(),
-                                      int(bool(to_level))), "mpk_permute_vectors")
+    """count blocks of n x nrhs elements (4- or 8-byte) between the caller's
+    numbering and the plan's level order (mpk_permute_vectors)."""
+    numel = int(count) * plan.n * plan.nrhs
+    sp, dp = _ptrs((src, numel, getattr(src, "dtype", None), "src"), (dst, numel, getattr(src, "dtype", None), "dst"))
+    _check(load().mpk_permute_vectors(plan.handle, sp, dp, int(count), src.element_size(), int(bool(to_level))),
+           "mpk_permute_vectors")
 
 
 def mpk_plan_last_error(plan: Plan):
@@ -384,8 +426,10 @@ def mpk_levels_noalloc(rowptr, col, root=0, level=None, stream=None, timeout_s=2
     n = rowptr.numel() - 1
     if level is None:
         level = torch.empty(n, dtype=torch.int32, device=rowptr.device)
+    rp, cp, lp = _ptrs((rowptr, n + 1, torch.int32, "rowptr"), (col, col.numel(), torch.int32, "col"),
+                       (level, n, torch.int32, "level"))
     nl = C.c_int32()
-    _check(load().mpk_levels_noalloc(n, col.numel(), _ptr(rowptr), _ptr(col), int(root), _ptr(level),
+    _check(load().mpk_levels_noalloc(n, col.numel(), rp, cp, int(root), lp,
                                      C.byref(nl), _stream(stream), float(timeout_s)), "mpk_levels_noalloc")
     return level, nl.value
 
@@ -402,8 +446,16 @@ class Batch:
             self.handle = None
 
 
-def _ptr_array(tensors):
-    return (C.c_void_p * len(tensors))(*[_ptr(t).value for t in tensors])
+def _batch_io(batch, xs, Ys):
+    """Per-plan input and output pointers, each checked against its plan."""
+    if len(xs) != len(batch.plans) or len(Ys) != len(batch.plans):
+        raise ValueError(f"expected {len(batch.plans)} inputs and outputs, one per plan")
+    specs = []
+    for pl, x, Y in zip(batch.plans, xs, Ys):
+        blk = pl.n * pl.nrhs
+        specs += [(x, blk, pl.vec_dtype, "x"), (Y, pl.p * blk, pl.vec_dtype, "Y")]
+    ps = [q.value for q in _ptrs(*specs)]
+    return (C.c_void_p * len(xs))(*ps[0::2]), (C.c_void_p * len(Ys))(*ps[1::2])
 
 
 def mpk_batch_create(plans) -> Batch:
@@ -422,12 +474,13 @@ def mpk_batch_info(batch: Batch):
 
 
 def mpk_batch_run(batch: Batch, xs, Ys, asynchronous=False):
-    _check(load().mpk_batch_run(batch.handle, _ptr_array(xs), _ptr_array(Ys), MPK_ASYNC if asynchronous else 0),
-           "mpk_batch_run")
+    px, py = _batch_io(batch, xs, Ys)
+    _check(load().mpk_batch_run(batch.handle, px, py, MPK_ASYNC if asynchronous else 0), "mpk_batch_run")
 
 
 def mpk_batch_graph_capture(batch: Batch, xs, Ys):
-    _check(load().mpk_batch_graph_capture(batch.handle, _ptr_array(xs), _ptr_array(Ys)), "mpk_batch_graph_capture")
+    px, py = _batch_io(batch, xs, Ys)
+    _check(load().mpk_batch_graph_capture(batch.handle, px, py), "mpk_batch_graph_capture")
 
 
 def mpk_batch_graph_launch(batch: Batch, asynchronous=False):
@@ -460,16 +513,28 @@ class Mlp:
         p = np.ascontiguousarray(params, dtype=np.float32)
         _check(load().mpk_mlp_set_params(self.handle, p.ctypes.data_as(C.c_void_p), p.size), "mpk_mlp_set_params")
 
+    def _batch(self, X):
+        import torch
+        if not isinstance(X, torch.Tensor) or X.dim() != 2:
+            raise TypeError("X: expected a 2-D torch.Tensor (batch x inputs)")
+        _want(X, X.shape[0] * self.shape[0], torch.float32, "X")
+        return X.shape[0]
+
     def forward(self, X):
         import torch
-        Y = torch.empty(X.shape[0], self.shape[2], dtype=torch.float32, device=X.device)
-        _check(load().mpk_mlp_forward(self.handle, _ptr(X), X.shape[0], _ptr(Y)), "mpk_mlp_forward")
+        b = self._batch(X)
+        Y = torch.empty(b, self.shape[2], dtype=torch.float32, device=X.device)
+        _check(load().mpk_mlp_forward(self.handle, _ptr(X), b, _ptr(Y)), "mpk_mlp_forward")
         return Y
 
     def loss_grad(self, X, T, M, want_grad=False):
+        import torch
+        b = self._batch(X)
+        xp, tp, mp = _ptrs((X, b * self.shape[0], torch.float32, "X"), (T, b * self.shape[2], torch.float32, "T"),
+                           (M, b * self.shape[2], torch.float32, "M"))
         loss = C.c_double()
         g = np.empty(self.num_params, dtype=np.float32) if want_grad else None
-        _check(load().mpk_mlp_loss_grad(self.handle, _ptr(X), _ptr(T), _ptr(M), X.shape[0], C.byref(loss),
+        _check(load().mpk_mlp_loss_grad(self.handle, xp, tp, mp, b, C.byref(loss),
                                         g.ctypes.data_as(C.c_void_p) if want_grad else None), "mpk_mlp_loss_grad")
         return (loss.value, g) if want_grad else loss.value
 

@@ -98,3 +98,21 @@ def test_one_very_wide_row_and_dense_block():
     D = mi.random_sparse(64, 1.0, 9)   # fully dense 64 x 64
     _check(D, 5, tol=1e-12)
     _check(D, 5, tol=1e-12, tune=mpk.MPK_TUNE_RESIDENT)
+
+
+def test_binding_rejects_mismatched_cuda_tensors():
+    """A CUDA tensor of the wrong size or dtype never reaches a kernel: the
+    binding raises before the launch, and the plan stays usable."""
+    A = mi.laplace2d(16)
+    plan = plan_of(A, 3, prec="f64")
+    x = torch.rand(A.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        mpk.mpk_run(plan, x[:-1], torch.empty(3, A.n, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        mpk.mpk_run(plan, x, torch.empty(2, A.n, dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError):
+        mpk.mpk_run(plan, x.float(), torch.empty(3, A.n, dtype=torch.float32, device="cuda"))
+    Y = torch.empty(3, A.n, dtype=torch.float64, device="cuda")
+    mpk.mpk_run(plan, x, Y)
+    ref = oracle.mpk(A, x.cpu().numpy(), 3)
+    assert np.all(rel_errors(Y.cpu().numpy(), ref) <= 1e-12)
