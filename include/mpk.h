@@ -203,6 +203,19 @@ int mpk_plan_schedule(mpk_plan_t plan, int32_t *work, int32_t *dep_lo, int32_t *
  * incomplete), MPK_ERR_OOM (first unpermuted run on a large matrix).      */
 int mpk_run(mpk_plan_t plan, const void *x, void *Y, uint32_t flags);
 
+/* mpk_run with x and Y in HOST memory (same layouts and flags): x is copied
+ * to the device, the level-blocked MPK runs, and each power is copied back
+ * as soon as it is in the caller's numbering, its copy overlapping the
+ * reordering of the next one.  Host memory should be page-locked
+ * (cudaHostAlloc / cudaHostRegister, or a pinned torch tensor) for the
+ * copies to run at link speed and overlap; pageable memory is accepted.
+ * The copies use the plan's stream and a second stream of the plan; the
+ * plan's stream waits for both, so with MPK_ASYNC synchronising the plan's
+ * stream is enough before Y is read.  Device buffers are plan-owned
+ * ((p + 3) blocks of n x nrhs elements, kept for later calls).  Errors as
+ * mpk_run.                                                                 */
+int mpk_run_host(mpk_plan_t plan, const void *x_host, void *Y_host, uint32_t flags);
+
 /* Baseline MPK (Sec. 3.1, Fig. 1): p back-to-back SpMV launches over the
  * same packed matrix, y_k = A y_{k-1}.  Same arguments and results as
  * mpk_run; it is the comparator the level-blocked kernel is measured

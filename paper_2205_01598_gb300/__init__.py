@@ -119,6 +119,7 @@ def load(path: str | None = None):
             "mpk_plan_perm": ([vp, vp, vp, vp, vp], C.c_int),
             "mpk_plan_schedule": ([vp, vp, vp, vp], C.c_int),
             "mpk_run": ([vp, vp, vp, u32], C.c_int),
+            "mpk_run_host": ([vp, vp, vp, u32], C.c_int),
             "mpk_baseline_run": ([vp, vp, vp, u32], C.c_int),
             "mpk_gershgorin": ([vp, C.POINTER(f64), C.POINTER(f64)], C.c_int),
             "mpk_cheb_coeffs_schroedinger": ([i32, f64, f64, f64, vp], C.c_int),
@@ -343,6 +344,21 @@ def mpk_run(plan: Plan, x, Y, permuted=False, asynchronous=False):
     p x n x nrhs, both in the plan's vector precision."""
     xp, yp = _mpk_io(plan, x, Y)
     _check(load().mpk_run(plan.handle, xp, yp, _flags(permuted, asynchronous)), "mpk_run")
+
+
+def mpk_run_host(plan: Plan, x, Y, permuted=False, asynchronous=False):
+    """mpk_run with x (n x nrhs) and Y (p x n x nrhs) in HOST memory
+    (mpk_run_host): the library copies x in and every power out, overlapping
+    the copies with the reordering.  Pinned CPU tensors give full-speed,
+    overlapped copies; with asynchronous=True synchronise the plan's stream
+    before reading Y."""
+    blk = plan.n * plan.nrhs
+    for t, numel, name in ((x, blk, "x"), (Y, plan.p * blk, "Y")):
+        _want(t, numel, plan.vec_dtype, name)
+        if t.is_cuda or not t.is_contiguous():
+            raise TypeError(f"{name}: expected a contiguous CPU tensor")
+    _check(load().mpk_run_host(plan.handle, C.c_void_p(x.data_ptr()), C.c_void_p(Y.data_ptr()),
+                               _flags(permuted, asynchronous)), "mpk_run_host")
 
 
 def mpk_baseline_run(plan: Plan, x, Y, permuted=False, asynchronous=False):

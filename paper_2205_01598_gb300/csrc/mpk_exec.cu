@@ -1373,17 +1373,18 @@ __global__ void k_gersh(ExecArgs a, double *out) {
     }
 }
 
-// dst[r] = src[perm[r]] (to_level) or dst[perm[r]] = src[r], in 4-byte words
-__global__ void k_permute(int32_t n, int32_t words, int32_t count, const int32_t *perm, const uint32_t *src,
-                          uint32_t *dst, int to_level) {
-    const int64_t per = (int64_t)n * words;
-    const int64_t total = per * count;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = g / per, rem = g % per;
-        const int32_t r = (int32_t)(rem / words), w = (int32_t)(rem % words);
-        const int64_t o = (int64_t)perm[r] * words + w;
-        if (to_level) dst[b * per + rem] = src[b * per + o];
-        else dst[b * per + o] = src[b * per + rem];
+// dst[r] = src[idx[r]] for the n rows of block blockIdx.y (rows of wpr
+// words of type W: 4, 8 or 16 bytes).  Both directions of the level
+// permutation are gathers (idx = perm into level order, iperm out of it):
+// the stores are coalesced, and the scattered loads of one block (one
+// vector) find its lines in L2, where consecutive blocks follow.
+template <typename W>
+__global__ void k_permute(int32_t n, int32_t wpr, const int32_t *__restrict__ idx, const W *__restrict__ src,
+                          W *__restrict__ dst) {
+    const int64_t base = (int64_t)blockIdx.y * n * wpr;
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int64_t from = base + (int64_t)__ldg(idx + r) * wpr, to = base + (int64_t)r * wpr;
+        for (int32_t w = 0; w < wpr; w++) dst[to + w] = src[from + w];
     }
 }
 
@@ -1609,13 +1610,26 @@ int ensure_io(Plan *pl, size_t bytes) {
 
 int permute_vectors(Plan *pl, const void *src, void *dst, int32_t count, int32_t elem_bytes, int32_t to_level,
                     cudaStream_t st) {
-    const int32_t words = pl->nrhs * elem_bytes / 4;
-    const int64_t total = (int64_t)pl->n * words * count;
-    if (total == 0) return MPK_OK;
-    unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)pl->num_sms * 16);
-    k_permute<<<grid, 256, 0, st>>>(pl->n, words, count, pl->d_perm, (const uint32_t *)src, (uint32_t *)dst,
-                                    to_level);
-    MPK_CUDA(cudaGetLastError());
+    const int32_t row_bytes = pl->nrhs * elem_bytes;
+    if ((uintptr_t)src % 4 || (uintptr_t)dst % 4) return MPK_ERR_INVALID;   // elements are 4 or 8 bytes
+    if ((int64_t)pl->n * count == 0) return MPK_OK;
+    const int32_t *idx = to_level ? pl->d_perm : pl->d_iperm;
+    // widest word that divides the row and both base addresses
+    const uintptr_t align = (uintptr_t)src | (uintptr_t)dst | (uintptr_t)row_bytes;
+    const size_t blk_bytes = (size_t)pl->n * row_bytes;
+    for (int32_t b0 = 0; b0 < count; b0 += 65535) {   // grid rows: one per vector block
+        const char *s = (const char *)src + blk_bytes * (size_t)b0;
+        char *d = (char *)dst + blk_bytes * (size_t)b0;
+        const dim3 grid((unsigned)std::min<int64_t>((pl->n + 255) / 256, (int64_t)pl->num_sms * 8),
+                        (unsigned)std::min(count - b0, 65535));
+        if (align % 16 == 0)
+            k_permute<uint4><<<grid, 256, 0, st>>>(pl->n, row_bytes / 16, idx, (const uint4 *)s, (uint4 *)d);
+        else if (align % 8 == 0)
+            k_permute<uint2><<<grid, 256, 0, st>>>(pl->n, row_bytes / 8, idx, (const uint2 *)s, (uint2 *)d);
+        else
+            k_permute<uint32_t><<<grid, 256, 0, st>>>(pl->n, row_bytes / 4, idx, (const uint32_t *)s, (uint32_t *)d);
+        MPK_CUDA(cudaGetLastError());
+    }
     return MPK_OK;
 }
 
@@ -1654,6 +1668,45 @@ int mpk_run(mpk_plan_t plan, const void *x, void *Y, uint32_t flags) {
     MPK_CUDA(cudaGetLastError());
     if (flags & MPK_ASYNC) return MPK_OK;
     return read_device_error(pl, pl->stream);
+}
+
+int mpk_run_host(mpk_plan_t plan, const void *x_host, void *Y_host, uint32_t flags) {
+    if (!plan || !x_host || !Y_host) return MPK_ERR_INVALID;
+    Plan *pl = &plan->pl;
+    cudaStream_t st = pl->stream;
+    const int eb = elem_bytes_of(pl);
+    const size_t blk = (size_t)pl->n * pl->nrhs * eb;
+    const bool level_io = flags & MPK_IO_PERMUTED;
+    int rc = ensure_io(pl, blk * (size_t)(pl->p + 3));
+    if (rc) return rc;
+    if (!pl->copy_stream) MPK_CUDA(cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : pl->io_ev)
+        if (!e) MPK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    char *xb = (char *)pl->d_io, *yb = xb + blk, *stage = yb + blk * (size_t)pl->p;
+    // input: host -> device, into level order
+    MPK_CUDA(cudaMemcpyAsync(level_io ? xb : stage, x_host, blk, cudaMemcpyHostToDevice, st));
+    if (!level_io && (rc = permute_vectors(pl, stage, xb, 1, eb, 1, st))) return rc;
+    if ((rc = launch_wavefront(pl, xb, yb, st))) return rc;
+    // outputs: each power into the caller's numbering (two staging blocks,
+    // alternating), then device -> host on the copy stream
+    for (int32_t k = 0; k < pl->p; k++) {
+        const char *src = yb + blk * (size_t)k;
+        if (!level_io) {
+            char *sb = stage + blk * (size_t)(k & 1);
+            if (k >= 2) MPK_CUDA(cudaStreamWaitEvent(st, pl->io_ev[2 + (k & 1)], 0));   // copy of power k-2 done
+            if ((rc = permute_vectors(pl, src, sb, 1, eb, 0, st))) return rc;
+            src = sb;
+        }
+        MPK_CUDA(cudaEventRecord(pl->io_ev[k & 1], st));
+        MPK_CUDA(cudaStreamWaitEvent(pl->copy_stream, pl->io_ev[k & 1], 0));
+        MPK_CUDA(cudaMemcpyAsync((char *)Y_host + blk * (size_t)k, src, blk, cudaMemcpyDeviceToHost,
+                                 pl->copy_stream));
+        MPK_CUDA(cudaEventRecord(pl->io_ev[2 + (k & 1)], pl->copy_stream));
+    }
+    // the plan's stream covers the copies too
+    MPK_CUDA(cudaStreamWaitEvent(st, pl->io_ev[2 + ((pl->p - 1) & 1)], 0));
+    if (flags & MPK_ASYNC) return MPK_OK;
+    return read_device_error(pl, st);
 }
 
 int mpk_baseline_run(mpk_plan_t plan, const void *x, void *Y, uint32_t flags) {

@@ -101,6 +101,8 @@ struct Plan {
     int32_t *d_ctl = nullptr;          // CTL_WORDS control words
     void *d_io = nullptr;              // permuted copies for unpermuted I/O (lazily)
     size_t io_bytes = 0;
+    cudaStream_t copy_stream = nullptr;   // device-to-host copies of mpk_run_host (lazily)
+    cudaEvent_t io_ev[4] = {};            // staging buffers unpermuted [0..1] / copied out [2..3]
     void *d_cheb = nullptr;            // Chebyshev vector ring (lazily)
     size_t cheb_bytes = 0;
 };

@@ -583,6 +583,9 @@ void free_plan(Plan *pl) {
                   pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec};
     for (void *p : ps)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : pl->io_ev)
+        if (e) cudaEventDestroy(e);
+    if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
 }
 
 int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {

@@ -69,3 +69,15 @@ def test_batch_checks_each_member():
         mpk.mpk_batch_run(b, [torch.zeros(4, dtype=f64), torch.zeros(3, dtype=f64)],
                           [torch.zeros(8, dtype=f64), torch.zeros(14, dtype=f64)])
     b.handle = None
+
+
+def test_run_host_checks():
+    pl = _plan(n=7, p=2, nrhs=1)
+    f64 = torch.float64
+    with pytest.raises(ValueError, match="Y: expected 14 elements"):
+        mpk.mpk_run_host(pl, torch.zeros(7, dtype=f64), torch.zeros(13, dtype=f64))
+    with pytest.raises(TypeError, match="contiguous CPU tensor"):
+        mpk.mpk_run_host(pl, torch.zeros(7, dtype=f64), torch.zeros(2, 14, dtype=f64)[:, ::2])
+    with pytest.raises(mpk.MpkError) as e:   # reaches the library, which refuses a NULL plan
+        mpk.mpk_run_host(pl, torch.zeros(7, dtype=f64), torch.zeros(2, 7, dtype=f64))
+    assert e.value.code == mpk.MPK_ERR_INVALID
