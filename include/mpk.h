@@ -256,6 +256,16 @@ int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
  * I_0 + 2 sum_k I_k = e^z.  MPK_ERR_INVALID if M < 0, r <= 0 or tau < 0.   */
 int mpk_cheb_coeffs_heat(int32_t M, double c, double r, double tau, double *coef);
 
+/* Host helper: the M+1 real coefficients (HOST memory) of A^{-1} =
+ * sum_k coef_k T_k((A - c)/r) for a symmetric A with spectrum in
+ * [c - r, c + r], c > r >= 0 (positive definite): with s = sqrt(c^2 - r^2)
+ * and q = r / (c + s) < 1, coef_0 = 1/s and coef_k = 2 (-q)^k / s.  The
+ * truncation after M terms errs by at most 2 q^{M+1} / (s (1 - q)) on the
+ * interval.  With mpk_cheb_real this applies a polynomial approximation of
+ * the inverse (a polynomial preconditioner, or a fixed-degree solve) in
+ * MPK sweeps.  MPK_ERR_INVALID unless M >= 0 and c > r >= 0.               */
+int mpk_cheb_coeffs_inverse(int32_t M, double c, double r, double *coef);
+
 /* Real Chebyshev propagation (the heat equation of Sec. 7): as mpk_cheb with
  * a plan of nrhs = 1, x and v_k real vectors of n entries in the plan
  * precision, coef M+1 real numbers (HOST memory), and y n DOUBLES.

@@ -201,6 +201,21 @@ def cheb_coeffs_heat(M, c, r, tau):
     return out
 
 
+def cheb_coeffs_inverse(M, c, r, nodes=4096):
+    """Coefficients (M+1,) of 1/lambda on [c-r, c+r] in T_k((lambda-c)/r), the
+    approximate inverse that a polynomial preconditioner applies through the
+    MPK (Sec. 1 and Sec. 8 name polynomial preconditioning as an MPK
+    consumer; the expansion itself is the textbook Chebyshev series of 1/x),
+    by Chebyshev-Gauss quadrature of f(t) = 1/(c + r t):
+    c_k = (2 - delta_k0)/N sum_j f(cos th_j) cos(k th_j), th_j = pi (j+1/2)/N."""
+    th = np.pi * (np.arange(nodes) + 0.5) / nodes
+    f = 1.0 / (c + r * np.cos(th))
+    k = np.arange(M + 1)
+    out = (np.cos(np.outer(k, th)) * f[None, :]).sum(1) / nodes
+    out[1:] *= 2.0
+    return out
+
+
 def cheb_real(A, coef, c, r, x):
     """y = sum_k coef_k T_k((A-c)/r) x for real x and coef (Eq. 7-9), FP64."""
     lib = _load()

@@ -25,7 +25,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
-SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu"]
+SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu", "mpk_poly.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -126,6 +126,7 @@ def load(path: str | None = None):
             "mpk_cheb": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_real": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_coeffs_heat": ([i32, f64, f64, f64, vp], C.c_int),
+            "mpk_cheb_coeffs_inverse": ([i32, f64, f64, vp], C.c_int),
             "mpk_permute_vectors": ([vp, vp, vp, i32, i32, i32], C.c_int),
             "mpk_plan_destroy": ([vp], C.c_int),
             "mpk_strerror": ([C.c_int], C.c_char_p),
@@ -385,6 +386,15 @@ def mpk_cheb_coeffs_heat(M, c, r, tau) -> np.ndarray:
     out = np.empty(M + 1, dtype=np.float64)
     _check(load().mpk_cheb_coeffs_heat(int(M), float(c), float(r), float(tau), out.ctypes.data_as(C.c_void_p)),
            "mpk_cheb_coeffs_heat")
+    return out
+
+
+def mpk_cheb_coeffs_inverse(M, c, r) -> np.ndarray:
+    """Real coefficients (M+1,) of A^{-1} in T_k((A - c)/r) for a spectrum in
+    [c - r, c + r], c > r >= 0 (mpk_cheb_coeffs_inverse)."""
+    out = np.empty(M + 1, dtype=np.float64)
+    _check(load().mpk_cheb_coeffs_inverse(int(M), float(c), float(r), out.ctypes.data_as(C.c_void_p)),
+           "mpk_cheb_coeffs_inverse")
     return out
 
 
