@@ -273,6 +273,18 @@ int mpk_cheb_coeffs_inverse(int32_t M, double c, double r, double *coef);
 int mpk_cheb_real(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
                   const void *x, double *y, uint32_t flags);
 
+/* mpk_cheb and mpk_cheb_real with x and y in HOST memory (same layouts,
+ * coefficients and flags): x is copied to a stream-ordered device buffer,
+ * the propagation runs, and y is copied back, all on the plan's stream
+ * (page-locked host memory for full-speed copies; pageable is accepted).
+ * With MPK_ASYNC, synchronise the plan's stream before reading y.  Errors
+ * as the device forms, and MPK_ERR_OOM when the staging buffers cannot be
+ * allocated.                                                               */
+int mpk_cheb_host(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
+                  const void *x_host, double *y_host, uint32_t flags);
+int mpk_cheb_real_host(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
+                       const void *x_host, double *y_host, uint32_t flags);
+
 /* ---------------------------------------------------------------- batches
  * Several plans (different matrices, sizes, block widths nrhs and powers p)
  * run in ONE persistent wavefront launch: their issue orders (each the

@@ -25,7 +25,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
-SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu", "mpk_poly.cu"]
+SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu", "mpk_poly.cu",
+           "mpk_host.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -124,7 +125,9 @@ def load(path: str | None = None):
             "mpk_gershgorin": ([vp, C.POINTER(f64), C.POINTER(f64)], C.c_int),
             "mpk_cheb_coeffs_schroedinger": ([i32, f64, f64, f64, vp], C.c_int),
             "mpk_cheb": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
+            "mpk_cheb_host": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_real": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
+            "mpk_cheb_real_host": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_coeffs_heat": ([i32, f64, f64, f64, vp], C.c_int),
             "mpk_cheb_coeffs_inverse": ([i32, f64, f64, vp], C.c_int),
             "mpk_permute_vectors": ([vp, vp, vp, i32, i32, i32], C.c_int),
@@ -354,12 +357,10 @@ def mpk_run_host(plan: Plan, x, Y, permuted=False, asynchronous=False):
     overlapped copies; with asynchronous=True synchronise the plan's stream
     before reading Y."""
     blk = plan.n * plan.nrhs
-    for t, numel, name in ((x, blk, "x"), (Y, plan.p * blk, "Y")):
-        _want(t, numel, plan.vec_dtype, name)
-        if t.is_cuda or not t.is_contiguous():
-            raise TypeError(f"{name}: expected a contiguous CPU tensor")
-    _check(load().mpk_run_host(plan.handle, C.c_void_p(x.data_ptr()), C.c_void_p(Y.data_ptr()),
-                               _flags(permuted, asynchronous)), "mpk_run_host")
+    _want(Y, plan.p * blk, plan.vec_dtype, "Y")
+    xp = _host_vec(x, blk, plan.vec_dtype, "x")
+    yp = _host_vec(Y, plan.p * blk, plan.vec_dtype, "Y")
+    _check(load().mpk_run_host(plan.handle, xp, yp, _flags(permuted, asynchronous)), "mpk_run_host")
 
 
 def mpk_baseline_run(plan: Plan, x, Y, permuted=False, asynchronous=False):
@@ -422,6 +423,35 @@ def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False, o
     _check(load().mpk_cheb(plan.handle, ci.ctypes.data_as(C.c_void_p), coef.shape[0] - 1, float(c), float(r),
                            xp, yp,
                            _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)), "mpk_cheb")
+
+
+def _host_vec(t, numel, dtype, name):
+    _want(t, numel, dtype, name)
+    if t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous CPU tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def mpk_cheb_host(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False):
+    """mpk_cheb with x (n, 2) and y (n, 2) float64 in HOST memory (mpk_cheb_host)."""
+    import torch
+    coef = np.asarray(coef, dtype=np.complex128)
+    ci = np.empty(2 * coef.shape[0], dtype=np.float64)
+    ci[0::2], ci[1::2] = coef.real, coef.imag
+    xp = _host_vec(x, plan.n * plan.nrhs, plan.vec_dtype, "x")
+    yp = _host_vec(y, plan.n * plan.nrhs, torch.float64, "y")
+    _check(load().mpk_cheb_host(plan.handle, ci.ctypes.data_as(C.c_void_p), coef.shape[0] - 1, float(c), float(r),
+                                xp, yp, _flags(permuted, asynchronous)), "mpk_cheb_host")
+
+
+def mpk_cheb_real_host(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False):
+    """mpk_cheb_real with x (n,) and y (n,) float64 in HOST memory (mpk_cheb_real_host)."""
+    import torch
+    ci = np.ascontiguousarray(coef, dtype=np.float64)
+    xp = _host_vec(x, plan.n * plan.nrhs, plan.vec_dtype, "x")
+    yp = _host_vec(y, plan.n * plan.nrhs, torch.float64, "y")
+    _check(load().mpk_cheb_real_host(plan.handle, ci.ctypes.data_as(C.c_void_p), ci.shape[0] - 1, float(c),
+                                     float(r), xp, yp, _flags(permuted, asynchronous)), "mpk_cheb_real_host")
 
 
 def mpk_permute_vectors(plan: Plan, src, dst, count, to_level):

@@ -1,9 +1,10 @@
-"""GPU parity of mpk_run_host: the MPK with x and Y in host memory, the
-copies overlapped with the reordering of each power.  The device work is
-that of mpk_run, so the results equal mpk_run's bit for bit, and the
-oracle's within the usual bars; pinned and pageable host memory, both
-orders of the vectors, the asynchronous form, and repeated calls (the
-staging buffers alternate between powers and calls)."""
+"""GPU parity of the host-buffer entry points (the device work between two
+copies, so the results equal the device forms' bit for bit):
+- mpk_run_host: the MPK, the copies overlapped with the reordering of each
+  power; also against the oracle within the usual bars, with pinned and
+  pageable memory, both vector orders, the asynchronous form and repeated
+  calls (the staging blocks alternate between powers and calls);
+- mpk_cheb_host / mpk_cheb_real_host: the Chebyshev propagations."""
 import numpy as np
 import pytest
 import torch
@@ -78,3 +79,29 @@ def test_unaligned_vectors_permute_with_narrow_words():
     mpk.mpk_run(plan, xbuf[1:], Y)
     ref = oracle.mpk(A, x.astype(np.float64), 3)
     assert np.all(rel_errors(Y.cpu().double().numpy(), ref) <= 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["f64", "bf16val"])
+@pytest.mark.parametrize("permuted", [False, True])
+def test_cheb_host_equals_device(prec, permuted):
+    """mpk_cheb_host / mpk_cheb_real_host: the device propagation between a
+    host-to-device and a device-to-host copy, bit-identical to the device form."""
+    A = mi.anderson3d(10, seed=8)
+    for G in (2, 1):
+        plan = plan_of(A, 4, prec=prec, nrhs=G)
+        lo, hi = mpk.mpk_gershgorin(plan)
+        c, r = (hi + lo) / 2, (hi - lo) / 2
+        dt = plan.vec_dtype
+        shape = (A.n, 2) if G == 2 else (A.n,)
+        x = torch.from_numpy(mi.uniform(5, A.n * G).reshape(shape)).to(dt)
+        yd = torch.empty(shape, dtype=torch.float64, device="cuda")
+        yh = torch.full(shape, float("nan"), dtype=torch.float64).pin_memory()
+        if G == 2:
+            coef = mpk.mpk_cheb_coeffs_schroedinger(21, c, r, 3.0 / r)
+            mpk.mpk_cheb(plan, coef, c, r, x.cuda(), yd, permuted=permuted)
+            mpk.mpk_cheb_host(plan, coef, c, r, x.pin_memory(), yh, permuted=permuted)
+        else:
+            coef = mpk.mpk_cheb_coeffs_heat(21, c, r, 3.0 / r)
+            mpk.mpk_cheb_real(plan, coef, c, r, x.cuda(), yd, permuted=permuted)
+            mpk.mpk_cheb_real_host(plan, coef, c, r, x, yh, permuted=permuted)   # pageable input
+        assert torch.equal(yh, yd.cpu())
