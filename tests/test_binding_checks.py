@@ -78,6 +78,7 @@ def test_run_host_checks():
         mpk.mpk_run_host(pl, torch.zeros(7, dtype=f64), torch.zeros(13, dtype=f64))
     with pytest.raises(TypeError, match="contiguous CPU tensor"):
         mpk.mpk_run_host(pl, torch.zeros(7, dtype=f64), torch.zeros(2, 14, dtype=f64)[:, ::2])
+    mpk.build()
     with pytest.raises(mpk.MpkError) as e:   # reaches the library, which refuses a NULL plan
         mpk.mpk_run_host(pl, torch.zeros(7, dtype=f64), torch.zeros(2, 7, dtype=f64))
     assert e.value.code == mpk.MPK_ERR_INVALID
