@@ -185,6 +185,27 @@ def time_oracle(A, x, p, budget_s=12.0):
     return 2.0 * A.nnz * p * reps / el / 1e9, reps, el
 
 
+def time_omp(A, x, p, budget_s=5.0):
+    """The multicore comparator: p back-to-back FP64 SpMVs with the rows split
+    statically over all OpenMP threads of the host (a reported baseline,
+    not the target), repeated until `budget_s`."""
+    import oracle
+    try:
+        _, threads = oracle.omp_pxspmv(A, x, 1)
+    except RuntimeError as e:
+        return {"unavailable": str(e)}
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.omp_pxspmv(A, x, p)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": round(2.0 * A.nnz * p * reps / el / 1e9, 4), "unit": "GFLOP/s", "cores": threads,
+            "kind": "p x SpMV, OpenMP static schedule, FP64 CRS",
+            "sample": f"full matrix, p={p}, {reps} runs in {el:.1f} s on {threads} threads"}
+
+
 def dist_setup(n_gpus, backend="nccl"):
     """Replicas under torchrun: one process per GPU (RANK / LOCAL_RANK /
     WORLD_SIZE / MASTER_* from the environment), no data-path collective;
@@ -348,11 +369,12 @@ def main():
               "frac_of_one_read_bound": round(value / (flops / (bytes_one_read / gbs) / 1e9), 4),
               "dram_bytes_per_nnz_per_power": round(traffic / (info["nnz"] * p), 3) if traffic else None,
               "hbm_gbs": peaks["hbm_gbs"], "peak_source": peak_src}
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and not args.no_cpu:
         gf, reps, el = time_oracle(A, x_host, p)
         cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"full matrix, p={p}, {reps} MPK runs in {el:.1f} s (sequential FP64 C)"}
+        cpu_omp = time_omp(A, x_host, p)
 
     clocks = sampler.summary()
     out = {
@@ -379,6 +401,7 @@ def main():
         "roofline": roof,
         "bounds": bounds,
         "cpu_baseline": cpu,
+        "cpu_pxspmv_openmp": cpu_omp,
         "clocks": clocks,
         "plan": {"ms": round(info["plan_ms"], 2), "spmv_equiv": round(info["plan_ms"] / (ms_base / p), 1),
                  "levels": info["n_levels"], "groups": info["n_groups"], "tiles": info["n_tiles"],

@@ -16,6 +16,8 @@ Functions and the passages of the paper they restate:
   lb_mpk               Sec. 4.2, Fig. 5 run sequentially (levels or level groups)
   gershgorin           spectral interval used for the Chebyshev scaling (Sec. 7)
   cheb_coeffs_schroedinger, cheb   Sec. 7, Eq. 7-9
+  omp_pxspmv           the multicore comparator (Sec. 6): Fig. 1 with rows split
+                       statically over OpenMP threads (mpk_omp.c, built apart)
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, dense brute force, the paper's worked examples and invariants.
@@ -46,6 +48,48 @@ def build(force: bool = False) -> str:
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+_OMP_SRC = os.path.join(_HERE, "mpk_omp.c")
+_OMP_PATH = os.path.join(_BUILD, "libomp_pxspmv.so")
+_omp_lib = None
+
+
+def build_omp(force: bool = False):
+    """Compile mpk_omp.c (gcc -fopenmp) into oracle/_build/libomp_pxspmv.so;
+    returns its path, or None when the compiler has no OpenMP."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_OMP_PATH) or os.path.getmtime(_OMP_PATH) < os.path.getmtime(_OMP_SRC):
+        tmp = _OMP_PATH + f".tmp{os.getpid()}"
+        r = subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+                            _OMP_SRC], capture_output=True)
+        if r.returncode != 0:
+            return None
+        os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
+def omp_pxspmv(A, x, p):
+    """p back-to-back FP64 SpMVs on all OpenMP threads of the host; returns
+    (Y, threads).  Raises RuntimeError when OpenMP is not available."""
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            path = build_omp()
+            if path is None:
+                raise RuntimeError("gcc without OpenMP: the multicore comparator is unavailable")
+            lib = C.CDLL(path)
+            i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+            lib.omp_pxspmv.argtypes = [C.c_int, i32p, i32p, f64p, C.c_int, f64p, f64p]
+            lib.omp_pxspmv.restype = None
+            lib.omp_pxspmv_threads.restype = C.c_int
+            _omp_lib = lib
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    Y = np.empty((p, A.n), dtype=np.float64)
+    _omp_lib.omp_pxspmv(A.n, np.ascontiguousarray(A.rowptr, dtype=np.int32), np.ascontiguousarray(A.col, dtype=np.int32),
+                        np.ascontiguousarray(A.val, dtype=np.float64), int(p), x, Y)
+    return Y, int(_omp_lib.omp_pxspmv_threads())
 
 
 def _load():
