@@ -85,3 +85,78 @@ def test_batch_rejects_mixed_precision():
     with pytest.raises(mpk.MpkError) as e:
         mpk.mpk_batch_create([p64, p32])
     assert e.value.code == mpk.MPK_ERR_UNSUPPORTED
+
+
+def _zipf_member(spec):
+    """Matrix of one batch member (module level, for the spawned pool)."""
+    m, seed, n = spec
+    return m, mi.zipf_graph(n, seed)
+
+
+def batch_specs(count=64, n_lo=20_000, n_hi=2_000_000):
+    """Members of the batched workload: (m, seed, N, nrhs, p) with N ~ U[n_lo, n_hi],
+    nrhs ~ U{1..16} and p ~ U{2..10} from SplitMix64 seed 1000 + m."""
+    specs = []
+    for m in range(count):
+        z = mi.splitmix64(1000 + m, 3)
+        n = n_lo + int(z[0] % np.uint64(n_hi - n_lo + 1))
+        specs.append((m, 1000 + m, n, 1 + int(z[1] % np.uint64(16)), 2 + int(z[2] % np.uint64(9))))
+    return specs
+
+
+def spmv_ref(A, v):
+    """A v in FP64 for v (n,) or (n, nrhs): the multicore comparator (bit-identical
+    to the oracle) one column at a time, else the oracle itself."""
+    cols = v.reshape(A.n, -1)
+    out = np.empty_like(cols)
+    for q in range(cols.shape[1]):
+        c = np.ascontiguousarray(cols[:, q])
+        try:
+            out[:, q] = oracle.omp_pxspmv(A, c, 1)[0][0]
+        except RuntimeError:
+            out[:, q] = oracle.mpk(A, c, 1)[0]
+    return out.reshape(v.shape)
+
+
+def check_powers(A, x, Y, tol):
+    """Every power of Y (p, n[, nrhs], original numbering) against an FP64 SpMV
+    of the previous one (the first against x): Y[k] = A Y[k-1] at any size."""
+    prev = x.astype(np.float64)
+    for k in range(Y.shape[0]):
+        ref = spmv_ref(A, prev)
+        got = Y[k].astype(np.float64)
+        assert np.max(np.abs(got - ref)) <= tol * max(np.max(np.abs(ref)), 1e-300), (k, A.n)
+        prev = got
+
+
+def test_batched_full_size_zipf64():
+    """The batched workload at full size in the benchmark's launch configuration:
+    64 Zipf-degree matrices, N ~ U[20k, 2M], nrhs ~ U{1..16}, p ~ U{2..10}, FP32,
+    one persistent launch replayed from a CUDA graph.  The oracle cannot run all
+    790M entries x powers in seconds, so every power of every member is checked
+    by the property that holds at any size, against FP64 SpMVs."""
+    import multiprocessing as mp
+    import os
+    specs = batch_specs()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        mats = dict(pool.map(_zipf_member, [(m, seed, n) for m, seed, n, _, _ in specs]))
+    plans, xs, Ys, perms, xh = [], [], [], [], []
+    for m, seed, n, nrhs, p in specs:
+        A = mats[m]
+        plan = plan_of(A, p, prec="f32", nrhs=nrhs)
+        perm = mpk.mpk_plan_perm(plan)[0].cpu().numpy()
+        x = mi.random_vector(A.n, 3000 + m, nrhs).astype(np.float32)
+        plans.append(plan)
+        perms.append(perm)
+        xh.append(x)
+        xs.append(torch.from_numpy(np.ascontiguousarray(x[perm])).cuda())
+        Ys.append(torch.full((p,) + x.shape, float("nan"), dtype=torch.float32, device="cuda"))
+    batch = mpk.mpk_batch_create(plans)
+    mpk.mpk_batch_graph_capture(batch, xs, Ys)
+    mpk.mpk_batch_graph_launch(batch)
+    torch.cuda.synchronize()
+    for (m, seed, n, nrhs, p), perm, x, Y in zip(specs, perms, xh, Ys):
+        Yl = Y.cpu().numpy()
+        Yo = np.empty_like(Yl)
+        Yo[:, perm] = Yl
+        check_powers(mats[m], x, Yo, 1e-5)
