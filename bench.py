@@ -30,7 +30,10 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 nominal (profiling recipe table); the FP64 MPK is ALU bound
+# Inputs whose working set is below this many bytes (twice the 136 MB L2 of a
+# GB300) get an L2 flush before every timed iteration.  The rule reads the
+# host matrix only, so both arms of the benchmark print the same config.
+L2_FLUSH_BELOW = 2 * 136_000_000
 
 CONFIGS = {
     # name: (generator, size, p, precision, description)
@@ -60,7 +63,85 @@ def make_matrix(kind, size):
     import mpk_inputs as mi
     if kind == "heat":
         return mi.star3d(size, 2)   # order-4 star stencil (Tab. 3)
+    if kind == "anderson3d":
+        return mi.anderson3d(size, W=16.5, seed=42)
     return getattr(mi, kind)(size)
+
+
+def vec_bytes(prec):
+    return 8 if prec == "f64" else 4
+
+
+def mpk_config(desc, A, p, prec):
+    """The config dict of an MPK line, computed from the host matrix alone
+    (identical in both arms)."""
+    ws = A.nnz * (vec_bytes(prec) + 4) + (p + 1) * A.n * vec_bytes(prec)
+    l2 = (f"inputs larger than L2 (working set {ws / 1e6:.0f} MB)" if ws > L2_FLUSH_BELOW else
+          "L2 flushed before every timed iteration (256 MB write outside the timing)")
+    return {"workload": desc, "n": A.n, "nnz": A.nnz, "p": p, "prec": prec, "io": "level order (permuted space)",
+            "l2": l2, "data": "synthetic"}
+
+
+def cheb_config(desc, A, p, prec):
+    return {"workload": desc, "n": A.n, "nnz": A.nnz, "p": p, "prec": prec, "M": CHEB_M, "r_dt": CHEB_RDT,
+            "io": "level order (permuted space)", "l2": "inputs larger than L2", "data": "synthetic"}
+
+
+def one_read_bytes(nnz, n, p, prec, nrhs=1):
+    """Algorithmic bytes of one MPK (the one-matrix-read lower bound): the
+    packed matrix once (value + 32-bit column per entry), the row pointers,
+    x and the p outputs."""
+    vb = vec_bytes(prec)
+    return nnz * (vb + 4) + 4 * (n + 1) + vb * n * nrhs * (1 + p)
+
+
+def pxspmv_bytes(nnz, n, p, prec, nrhs=1):
+    """Algorithmic bytes of p back-to-back SpMVs: the matrix, the row pointers,
+    the input and the output once per power."""
+    vb = vec_bytes(prec)
+    return p * (nnz * (vb + 4) + 4 * n + 2 * vb * n * nrhs)
+
+
+def cheb_sweep_bytes(kind, nnz, n, prec, cols):
+    """Algorithmic bytes of one Chebyshev sweep of p powers: the matrix once
+    (BF16 off-diagonal values, 32-bit columns and the FP32 diagonal in the
+    BF16 form; value + column per entry otherwise), the two state vectors
+    read at the start and the two written at the end, and the FP64
+    coefficient sum read and written once."""
+    vb = vec_bytes(prec)
+    if prec == "bf16val":
+        off = nnz - n
+        matrix = off * (2 + 4) + n * 4
+    else:
+        matrix = nnz * (vb + 4)
+    return matrix + 4 * n * cols * vb + 2 * n * cols * 8
+
+
+def fma_rate(mpk, torch, prec, iters):
+    """Sustained FMA rate (TFLOP/s) of the library's FMA-chain probe in `prec`,
+    timed with CUDA events on the current stream (best of 3 after a warm-up)."""
+    sink = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    mpk.mpk_probe_fma(prec, sink, iters=iters)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fl = mpk.mpk_probe_fma(prec, sink, iters=iters)
+        e1.record(st)
+        torch.cuda.synchronize()
+        rate = fl / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        best = rate if best is None else max(best, rate)
+    return best
+
+
+def per_power_errors(got, ref):
+    """Relative infinity-norm error of every power: ||got_k - ref_k|| / ||ref_k||."""
+    out = []
+    for k in range(ref.shape[0]):
+        den = float(np.max(np.abs(ref[k])))
+        out.append(float(np.max(np.abs(got[k] - ref[k]))) / (den if den > 0 else 1e-300))
+    return out
 
 
 def kernel_sources_hash():
@@ -251,13 +332,10 @@ def main():
     if args.config in BATCH_CONFIGS:
         return run_batch(args)
     kind, size, p, prec, desc = CONFIGS[args.config]
-    cfg = {"workload": desc, "n": None, "nnz": None, "p": p, "prec": prec,
-           "io": "level order (permuted space)", "l2": "inputs larger than L2", "data": "synthetic"}
-
     if args.impl == "reference":
-        return run_reference(args, kind, size, p, cfg)
+        return run_reference(args, kind, size, p, prec, desc)
     if kind in ("anderson3d", "heat"):
-        return run_cheb(args, kind, size, p, prec, cfg)
+        return run_cheb(args, kind, size, p, prec, desc)
 
     import torch
     import mpk_inputs as mi
@@ -268,7 +346,7 @@ def main():
     mpk.load()
 
     A = make_matrix(kind, size)
-    cfg["n"], cfg["nnz"] = A.n, A.nnz
+    cfg = mpk_config(desc, A, p, prec)
     flops = 2.0 * A.nnz * p
     rp, cl, va = mpk.csr_to_device(A)
     plan = mpk.mpk_plan(rp, cl, va, p, prec=prec)
@@ -280,13 +358,12 @@ def main():
     Y = torch.empty(p, A.n, dtype=vdt, device="cuda")
     st = torch.cuda.current_stream()
 
-    # inputs smaller than L2: every timed iteration starts from a flushed L2
-    # (a 256 MB write outside the iteration's events)
-    working_set = info["matrix_bytes"] + (p + 1) * A.n * (8 if prec == "f64" else 4)
+    # inputs smaller than twice the L2: every timed iteration starts from a
+    # flushed L2 (a 256 MB write outside the iteration's events)
     l2 = torch.cuda.get_device_properties(0).L2_cache_size
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if working_set <= 2 * l2 else None
-    cfg["l2"] = (f"inputs larger than L2 (working set {working_set / 1e6:.0f} MB, L2 {l2 / 1e6:.0f} MB)"
-                 if flush is None else "L2 flushed before every timed iteration (256 MB write outside the timing)")
+    ws_bytes = A.nnz * (vec_bytes(prec) + 4) + (p + 1) * A.n * vec_bytes(prec)
+    need_flush = ws_bytes <= L2_FLUSH_BELOW or ws_bytes <= 2 * l2
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if need_flush else None
 
     def timed(fn, steps, warmup, sampler=None):
         for _ in range(warmup):
@@ -324,6 +401,7 @@ def main():
     ms = timed(lambda: mpk.mpk_run(plan, x, Y, permuted=True, asynchronous=True), args.steps, args.warmup, sampler)
     mpk.mpk_run(plan, x, Y, permuted=True)   # synchronous call: surfaces any device-side error
     value = whole_job_value(flops, ws, ms)
+    Y_level = Y.cpu().numpy().astype(np.float64)
 
     # baseline: p back-to-back SpMVs over the same packed matrix, same GPU
     ms_base = timed(lambda: mpk.mpk_baseline_run(plan, x, Y, permuted=True, asynchronous=True),
@@ -341,40 +419,50 @@ def main():
     ms_e2e = timed(e2e_step, max(3, min(args.steps, 20)), 2)
     value_e2e = whole_job_value(flops, ws, ms_e2e)
 
+    # roofline of the dominant kernel (the wavefront, one launch per step):
+    # the one-read algorithmic bytes per launch over the launch time, against
+    # the measured HBM copy bandwidth; the FP64 pipe's share beside it,
+    # against the FP64 FMA rate measured in this process
     peaks, peak_src = load_peaks()
     traffic = recorded_traffic("k_wave_laplace3d160_p8.md", prec) if (kind, size, p) == ("laplace3d", 160, 8) else None
-    # the FP64 path is bound by FP64 arithmetic (1 FMA per stored entry and power)
-    if prec == "f64":
-        achieved = flops / (ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
-                "peak_source": "nominal FP64 rate of the profiling recipe"}
-    else:
-        vb = 4
-        alg_bytes = info["nnz"] * (vb + 4) + (A.n + 1) * 4 + A.n * vb * (1 + p)
-        achieved = alg_bytes / (ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                "peak_source": peak_src}
+    alg = one_read_bytes(info["nnz"], A.n, p, prec)
+    achieved = alg / (ms * 1e-3) / 1e9
+    fp64_rate = fma_rate(mpk, torch, "f64", 1 << 13)
+    fp32_rate = fma_rate(mpk, torch, "f32", 1 << 19)
+    pipe_rate = fp64_rate if prec == "f64" else fp32_rate
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+            "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_launch": int(alg),
+            "pipe": {"unit": "TFLOP/s", "achieved": round(flops / (ms * 1e-3) / 1e12, 4),
+                     "peak": round(pipe_rate, 4), "frac": round(flops / (ms * 1e-3) / 1e12 / pipe_rate, 4),
+                     "peak_source": f"measured in this run: {'FP64' if prec == 'f64' else 'FP32'} FMA-chain probe "
+                                    "(mpk_probe_fma), best of 3, CUDA events",
+                     "note": "one FMA (2 flops) per stored entry and power"}}
 
     # the two HBM bounds of the method: p back-to-back SpMVs streaming the
     # matrix p times, and one read of the matrix per MPK
-    vb = 8 if prec == "f64" else 4
-    bytes_pxspmv = p * (info["nnz"] * (vb + 4) + 4 * A.n + 2 * vb * A.n)
-    bytes_one_read = info["nnz"] * (vb + 4) + 4 * (A.n + 1) + vb * A.n * (1 + p)
+    bytes_pxspmv = pxspmv_bytes(info["nnz"], A.n, p, prec)
     gbs = peaks["hbm_gbs"] * 1e9
     bounds = {"pxspmv_hbm_gflops": round(flops / (bytes_pxspmv / gbs) / 1e9, 1),
-              "one_read_hbm_gflops": round(flops / (bytes_one_read / gbs) / 1e9, 1),
+              "one_read_hbm_gflops": round(flops / (alg / gbs) / 1e9, 1),
               "frac_of_pxspmv_bound": round(value / (flops / (bytes_pxspmv / gbs) / 1e9), 4),
-              "frac_of_one_read_bound": round(value / (flops / (bytes_one_read / gbs) / 1e9), 4),
+              "frac_of_one_read_bound": round(value / (flops / (alg / gbs) / 1e9), 4),
               "dram_bytes_per_nnz_per_power": round(traffic / (info["nnz"] * p), 3) if traffic else None,
-              "hbm_gbs": peaks["hbm_gbs"], "peak_source": peak_src}
-    cpu = cpu_omp = None
-    if rank == 0 and not args.no_cpu:
-        gf, reps, el = time_oracle(A, x_host, p)
-        cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": f"full matrix, p={p}, {reps} MPK runs in {el:.1f} s (sequential FP64 C)"}
-        cpu_omp = time_omp(A, x_host, p)
+              "hbm_gbs": peaks["hbm_gbs"], "peak_source": peak_src,
+              "fp64_fma_tflops_measured": round(fp64_rate, 4), "fp32_fma_tflops_measured": round(fp32_rate, 3)}
+    cpu = cpu_omp = err = None
+    if rank == 0:
+        import oracle
+        ref = oracle.mpk(A, x_host, p)
+        got = np.empty_like(Y_level)
+        got[:, perm.cpu().numpy().astype(np.int64)] = Y_level
+        err = [float("%.3e" % e) for e in per_power_errors(got, ref)]
+        if not args.no_cpu:
+            gf, reps, el = time_oracle(A, x_host, p)
+            cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                   "sample": f"full matrix, p={p}, {reps} MPK runs in {el:.1f} s (sequential FP64 C)"}
+            cpu_omp = time_omp(A, x_host, p)
 
     clocks = sampler.summary()
     out = {
@@ -391,6 +479,8 @@ def main():
         "dtype": {"f64": "f64", "f32": "f32"}[prec],
         "data": "synthetic",
         "config": cfg,
+        "error_vs_fp64_oracle": {"per_power": err, "max": max(err) if err else None,
+                                 "norm": "relative infinity norm, ||Y_k - A^k x|| / ||A^k x|| per power k"},
         "speedup_vs_pxspmv": round(ms_base / ms, 4),
         "baseline_pxspmv": {"ms_per_step": round(ms_base, 5), "value": round(whole_job_value(flops, ws, ms_base), 3),
                             "gpu_launches_per_step": p},
@@ -403,6 +493,7 @@ def main():
         "cpu_baseline": cpu,
         "cpu_pxspmv_openmp": cpu_omp,
         "clocks": clocks,
+        "l2_flush": {"flushed": flush is not None, "device_l2_bytes": l2},
         "plan": {"ms": round(info["plan_ms"], 2), "spmv_equiv": round(info["plan_ms"] / (ms_base / p), 1),
                  "levels": info["n_levels"], "groups": info["n_groups"], "tiles": info["n_tiles"],
                  "tile_rows": info["tile_rows"], "grid_ctas": info["grid_ctas"],
@@ -412,6 +503,13 @@ def main():
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def batch_config(desc, specs):
+    """Config of a batched line (identical in both arms): the matrix count and
+    the total rows, right-hand sides and powers of the members."""
+    return {"workload": desc, "matrices": len(specs), "rows": int(sum(s[2] for s in specs)),
+            "rhs": int(sum(s[3] for s in specs)), "powers": int(sum(s[4] for s in specs)), "data": "synthetic"}
 
 
 def _gen_batch_member(spec):
@@ -498,9 +596,9 @@ def run_batch(args):
         "metric": "batched MPK GFLOP/s (sum 2*nnz*nrhs*p / t)", "value": round(flops / (ms * 1e-3) / 1e9, 3),
         "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "matrices": count, "rows": rows_total, "nnz": nnz_total,
-                   "gen_s": round(t_gen, 1), "plan_s": round(t_plan, 1), "items": binfo["n_items"],
-                   "grid_ctas": binfo["grid_ctas"]},
+        "config": batch_config(desc, specs),
+        "batch": {"nnz": nnz_total, "gen_s": round(t_gen, 1), "plan_s": round(t_plan, 1), "items": binfo["n_items"],
+                  "grid_ctas": binfo["grid_ctas"]},
         "speedup_vs_separate_launches": round(ms_sep / ms, 4),
         "speedup_vs_pxspmv": round(ms_base / ms, 4),
         "separate_launches": {"ms_per_step": round(ms_sep, 4), "gpu_launches_per_step": count},
@@ -511,7 +609,7 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
-def run_cheb(args, kind, size, p, prec, cfg):
+def run_cheb(args, kind, size, p, prec, desc):
     """Chebyshev time propagation (Sec. 7): one step = y = sum_k c_k T_k(Ahat) psi
     with M = 64 moments in sweeps of p powers.  Schroedinger (Anderson
     Hamiltonian, complex psi, Bessel coefficients) or heat equation (order-4
@@ -526,8 +624,8 @@ def run_cheb(args, kind, size, p, prec, cfg):
     mpk.load()
     heat = kind == "heat"
     G = 1 if heat else 2
-    A = mi.star3d(size, 2) if heat else mi.anderson3d(size, W=16.5, seed=42)
-    cfg.update({"n": A.n, "nnz": A.nnz, "M": CHEB_M, "r_dt": CHEB_RDT})
+    A = make_matrix(kind, size)
+    cfg = cheb_config(desc, A, p, prec)
     flops = 2.0 * A.nnz * G * CHEB_M
     rp, cl, va = mpk.csr_to_device(A)
     plan = mpk.mpk_plan(rp, cl, va, p, prec=prec, nrhs=G)
@@ -589,20 +687,26 @@ def run_cheb(args, kind, size, p, prec, cfg):
         run_host(plan, coef, c, r, xh_t, yh_t, asynchronous=True)
 
     ms_e2e = timed(e2e_step, max(3, min(args.steps, 10)), 2)
-    if heat and prec == "f64":
-        # FP64 throughout: one FMA per stored entry and power, plus about 6
-        # FP64 operations per row and power in the node body
-        fp64_flops = 2.0 * A.nnz * CHEB_M + 2.0 * 6 * A.n * CHEB_M
-        note = "nominal FP64 rate of the profiling recipe; achieved counts one FMA per entry and power plus the node body's 6 FP64 operations per row and power"
-    else:
-        # FP64 instructions per row and power in the node body (scaling with the
-        # diagonal, recurrence, complex coefficient sum): counted as FMAs (2 flops)
-        fp64_flops = 2.0 * 12 * A.n * CHEB_M
-        note = ("nominal FP64 rate of the profiling recipe; achieved counts the 12 FP64 "
-                "operations per row and power of the node body as FMAs")
-    achieved = fp64_flops / (ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "peak_source": note}
+    # roofline of the dominant kernel (the sweep, ceil(M/p) launches per
+    # step): the algorithmic bytes of a sweep times the sweeps of a step,
+    # over the step time, against the measured HBM copy bandwidth
+    peaks, peak_src = load_peaks()
+    sweeps = -(-CHEB_M // p)
+    alg = sweeps * cheb_sweep_bytes(kind, A.nnz, A.n, prec, G)
+    achieved = alg / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_step": int(alg),
+            "note": f"{sweeps} sweeps per step; per sweep the matrix once, two state vectors read and two "
+                    "written, the FP64 coefficient sum read and written"}
+    if prec == "f64":
+        fp64_rate = fma_rate(mpk, torch, "f64", 1 << 13)
+        tf = 2.0 * A.nnz * G * CHEB_M / (ms * 1e-3) / 1e12
+        roof["pipe"] = {"unit": "TFLOP/s", "achieved": round(tf, 4), "peak": round(fp64_rate, 4),
+                        "frac": round(tf / fp64_rate, 4),
+                        "peak_source": "measured in this run: FP64 FMA-chain probe (mpk_probe_fma)",
+                        "note": "SpMV flops only (2 per stored entry, column and power)"}
     cpu, err = None, None
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -614,7 +718,9 @@ def run_cheb(args, kind, size, p, prec, cfg):
         el = time.perf_counter() - t0
         yg = y_gpu.cpu().numpy()
         got = yg if heat else yg[:, 0] + 1j * yg[:, 1]
-        err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        err = {"result_relative": float("%.3e" % (np.max(np.abs(got - ref)) / np.max(np.abs(ref)))),
+               "input_relative": float("%.3e" % (np.max(np.abs(got - ref)) / np.max(np.abs(psi)))),
+               "norm": "infinity norm of y - y_oracle over that of y_oracle (result) and of the input (input)"}
         cpu = {"value": round(flops / el / 1e9, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                "sample": f"one full Chebyshev step (M={CHEB_M}) in {el:.1f} s (sequential FP64 C)"}
     out = {
@@ -627,7 +733,7 @@ def run_cheb(args, kind, size, p, prec, cfg):
         "e2e": {"value": round(whole_job_value(flops, ws, ms_e2e), 3), "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(np.prod(x.shape)) * xh_t.element_size(),
                 "d2h_bytes_per_step": int(np.prod(y.shape)) * 8, "ms_per_step": round(ms_e2e, 4)},
-        "gpu_launches": args.steps * (-(-CHEB_M // p) + 1), "roofline": roof, "cpu_baseline": cpu,
+        "gpu_launches": args.steps * (-(-CHEB_M // p) + 2), "roofline": roof, "cpu_baseline": cpu,
         "clocks": sampler.summary(),
         "plan": {"ms": round(info["plan_ms"], 2), "levels": info["n_levels"], "groups": info["n_groups"],
                  "tiles": info["n_tiles"], "val_bytes": info["val_bytes"], "matrix_bytes": info["matrix_bytes"]},
@@ -657,7 +763,7 @@ def _reference_line(args, metric, work, el, steps, warm, cfg, sample):
             "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_reference(args, kind, size, p, cfg):
+def run_reference(args, kind, size, p, prec, desc):
     """Reference arm: the FP64 CPU oracle (sequential C) on the host cores,
     rank 0 only; W untimed warm-up steps, then exactly K timed steps, each a
     bounded sample of the workload: one full MPK (MPK configs) or one sweep
@@ -670,7 +776,7 @@ def run_reference(args, kind, size, p, cfg):
     import oracle
     oracle.build()
     A = make_matrix(kind, size)
-    cfg["n"], cfg["nnz"] = A.n, A.nnz
+    cfg = cheb_config(desc, A, p, prec) if kind in ("anderson3d", "heat") else mpk_config(desc, A, p, prec)
     if kind in ("anderson3d", "heat"):
         lo, hi = oracle.gershgorin(A)
         if kind == "heat":   # -Delta is positive semi-definite: spectrum in [0, hi]
@@ -735,7 +841,7 @@ def run_batch_reference(args, specs, desc, count):
     for i in range(warm, warm + steps):
         work += step(i)
     el = time.perf_counter() - t0
-    cfg = {"workload": desc, "matrices": count, "data": "synthetic"}
+    cfg = batch_config(desc, specs)
     out = _reference_line(args, "batched MPK GFLOP/s (sum 2*nnz*nrhs*p / t)", work, el, steps, warm, cfg,
                           f"{steps} timed steps after {warm} warm-up; step i = the MPK of batch member i mod "
                           f"{count} with its nrhs and p (sequential FP64 C)")

@@ -401,10 +401,11 @@ int mpk_plan_debug_drop_flag(mpk_plan_t plan, int32_t tile, int32_t power);
 /* Levels of Eq. 3 (the same values as mpk_plan_perm's level[] for a plan
  * built with assume_symmetric != 0 and the same root) WITHOUT ANY DEVICE
  * ALLOCATION.  The paper has no counterpart: this entry point exists for
- * callers that must not allocate device memory, for example code running
- * inside a stream capture that is later replayed as a CUDA graph, or a host
- * that pre-sizes all device memory at start-up and forbids allocation
- * afterwards.  mpk_plan allocates, so such callers use this call.
+ * callers that must not allocate device memory, for example a host that
+ * sizes all device memory at start-up and forbids allocation afterwards
+ * (an embedded service under a fixed memory budget, or a process that
+ * shares the GPU under a hard quota).  mpk_plan allocates, so such callers
+ * use this call.
  *
  * The scratch (frontier queue and control words) is a static device array
  * inside this library, sized for n <= 1,048,576 vertices (about 4 MB, held
@@ -413,19 +414,34 @@ int mpk_plan_debug_drop_flag(mpk_plan_t plan, int32_t tile, int32_t power);
  * col[nnz] (DEVICE, caller-owned; the stored pattern is taken as symmetric),
  * the root, and level[n] (DEVICE, caller-allocated, overwritten).  *n_levels
  * (host) receives L_m.  stream: cudaStream_t; timeout_s bounds each wait of
- * the kernel (0 = 2 s).  The call synchronises the stream.
+ * the kernel (0 = 2 s).
  *
- * The first call on a device looks up the device address of the array (and
- * may load the library's device code), so make that first call before any
- * stream capture.  Every call shares the one array and clears its control
- * words on entry: calls that overlap on the GPU (other streams, other host
- * threads) race and must not be issued.
+ * The call synchronises the stream twice and reads a status word back to the
+ * host (the validation result and the level count), so it must not be
+ * issued on a stream that is being captured into a CUDA graph.  Each call
+ * looks up the device address of the array in the current device's context
+ * (which may load the library's device code on the first call).  Every call
+ * shares the one array and clears its control words on entry: calls that
+ * overlap on the GPU (other streams, other host threads) race and must not
+ * be issued.
  *
  * Errors: MPK_ERR_UNSUPPORTED if n > 1,048,576 (the scratch limit);
  * MPK_ERR_INVALID for NULL pointers, n < 1, a root outside [0, n) or a
  * malformed CRS (found on the device); MPK_ERR_TIMEOUT, MPK_ERR_CUDA.      */
 int mpk_levels_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int32_t *col, int32_t root,
                        int32_t *level, int32_t *n_levels, void *stream, double timeout_s);
+
+/* Arithmetic-rate probe for an ALU roofline (the paper measures its
+ * machine's limits with microbenchmarks too, Sec. 2): launches, on `stream`
+ * (cudaStream_t) and without waiting, SMs x blocks_per_sm CTAs of 256
+ * threads, each thread running 8 independent chains of `iters` dependent
+ * fused multiply-adds in FP64 (prec = MPK_F64) or FP32 (prec = MPK_F32).
+ * *flops (host) receives the flops of the launch (2 per FMA); the caller
+ * times the launch (CUDA events on the same stream) for the rate.  sink:
+ * DEVICE buffer of at least 8 bytes (never written in practice; it keeps
+ * the chains live).  MPK_ERR_INVALID for a NULL pointer, another prec,
+ * blocks_per_sm outside [1, 32], or iters not a positive multiple of 4.     */
+int mpk_probe_fma(int32_t prec, int32_t blocks_per_sm, int64_t iters, void *sink, void *stream, double *flops);
 
 /* Static description of a status code.                                     */
 const char *mpk_strerror(int status);

@@ -26,7 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
 SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu", "mpk_poly.cu",
-           "mpk_host.cu"]
+           "mpk_host.cu", "mpk_calib.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -137,6 +137,7 @@ def load(path: str | None = None):
             "mpk_plan_debug_drop_flag": ([vp, i32, i32], C.c_int),
             "mpk_levels_noalloc": ([i32, i64, vp, vp, i32, vp, C.POINTER(i32), vp, f64], C.c_int),
             "mpk_plan_features": ([vp, vp, i32], C.c_int),
+            "mpk_probe_fma": ([i32, i32, i64, vp, vp, C.POINTER(f64)], C.c_int),
             "mpk_mlp_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
             "mpk_mlp_num_params": ([vp], C.c_int32),
             "mpk_mlp_get_params": ([vp, vp, i32], C.c_int),
@@ -488,6 +489,18 @@ def mpk_levels_noalloc(rowptr, col, root=0, level=None, stream=None, timeout_s=2
     _check(load().mpk_levels_noalloc(n, col.numel(), rp, cp, int(root), lp,
                                      C.byref(nl), _stream(stream), float(timeout_s)), "mpk_levels_noalloc")
     return level, nl.value
+
+
+def mpk_probe_fma(prec, sink, blocks_per_sm=8, iters=1 << 14, stream=None):
+    """Launches the FMA-chain probe (mpk_probe_fma) on the stream without
+    waiting; returns its flop count.  prec "f64" or "f32"; sink: a CUDA
+    tensor of at least 8 bytes.  The caller times the launch."""
+    if not hasattr(sink, "is_cuda") or not sink.is_cuda or sink.numel() * sink.element_size() < 8:
+        raise TypeError("sink: expected a CUDA tensor of at least 8 bytes")
+    fl = C.c_double()
+    _check(load().mpk_probe_fma(PRECISIONS[prec], int(blocks_per_sm), int(iters), _ptr(sink), _stream(stream),
+                                C.byref(fl)), "mpk_probe_fma")
+    return fl.value
 
 
 class Batch:

@@ -1025,22 +1025,16 @@ static __device__ __align__(256) int32_t g_levels_scratch[kStaticCtlWords + kSta
 
 namespace {
 
-std::mutex g_levels_scratch_mu;
-int32_t *g_levels_scratch_dev[256] = {};   // device address of the array, per device
-
-// Device address of the static scratch on the current device (looked up once).
+// Device address of the static scratch in the current device's context.  It
+// is looked up on every call (cudaGetSymbolAddress is cheap): a cached
+// address would go stale once the primary context is torn down and created
+// again (cudaDeviceReset), and the kernels would then write through an
+// address the new context does not own.
 int static_levels_scratch(int32_t **out) {
-    int dev = 0;
-    MPK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return MPK_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_levels_scratch_mu);
-    if (!g_levels_scratch_dev[dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_levels_scratch);
-        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_levels_scratch)", __LINE__);
-        g_levels_scratch_dev[dev] = (int32_t *)ptr;
-    }
-    *out = g_levels_scratch_dev[dev];
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_levels_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_levels_scratch)", __LINE__);
+    *out = (int32_t *)ptr;
     return MPK_OK;
 }
 

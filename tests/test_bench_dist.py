@@ -49,7 +49,7 @@ def test_reference_arm_idles_outside_rank_zero(monkeypatch, capsys):
     import bench
     monkeypatch.setenv("RANK", "1")
     args = type("A", (), {"steps": 1, "warmup": 0})()
-    assert bench.run_reference(args, "laplace2d", 64, 4, {}) is None
+    assert bench.run_reference(args, "laplace2d", 64, 4, "f64", "2D 64^2") is None
     assert capsys.readouterr().out == ""
 
 
@@ -64,10 +64,49 @@ def test_reference_arm_times_exactly_k_steps(monkeypatch, capsys):
     monkeypatch.setattr(oracle, "mpk", lambda A, x, p: calls.append(p) or real(A, x, p))
     monkeypatch.setenv("RANK", "0")
     args = type("A", (), {"steps": 4, "warmup": 3})()
-    bench.run_reference(args, "laplace2d", 64, 4, {"workload": "2D 64^2"})
+    bench.run_reference(args, "laplace2d", 64, 4, "f64", "2D 64^2")
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert calls == [4] * 7
     assert line["impl"] == "reference" and line["steps"] == 4 and line["warmup"] == 3
     assert line["config"]["nnz"] == 20224 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_both_arms_print_the_same_config():
+    """The config dicts come from the host matrix alone, so the reference arm
+    and the GPU arm print identical ones (MPK, Chebyshev and batch lines)."""
+    import bench
+    import mpk_inputs as mi
+    A = mi.laplace2d(64)
+    c1 = bench.mpk_config("2D", A, 4, "f64")
+    assert c1 == bench.mpk_config("2D", mi.laplace2d(64), 4, "f64")
+    assert c1["l2"].startswith("L2 flushed")        # 0.4 MB working set
+    big = type("M", (), {"n": 4_096_000, "nnz": 28_518_400})()
+    assert bench.mpk_config("3D", big, 8, "f64")["l2"].startswith("inputs larger than L2")
+    specs = [(0, 1000, 25_000, 3, 4), (1, 1001, 30_000, 1, 2)]
+    assert bench.batch_config("b", specs) == {"workload": "b", "matrices": 2, "rows": 55_000, "rhs": 4,
+                                              "powers": 6, "data": "synthetic"}
+
+
+def test_algorithmic_bytes_of_the_headline_workload():
+    """The one-read and p x SpMV bytes of the 3D 160^3 p = 8 workload
+    (653.5 MB and 3.39 GB in FP64, 392 MB and 2.22 GB in FP32), and the
+    Anderson sweep (about 833 MB with BF16 hoppings)."""
+    import bench
+    n, nnz = 4_096_000, 28_518_400
+    assert bench.one_read_bytes(nnz, n, 8, "f64") == pytest.approx(653.5e6, rel=1e-3)
+    assert bench.pxspmv_bytes(nnz, n, 8, "f64") == pytest.approx(3.393e9, rel=1e-3)
+    assert bench.one_read_bytes(nnz, n, 8, "f32") == pytest.approx(392.0e6, rel=2e-3)
+    assert bench.pxspmv_bytes(nnz, n, 8, "f32") == pytest.approx(2.218e9, rel=1e-3)
+    sweep = bench.cheb_sweep_bytes("anderson3d", 56_000_000, 8_000_000, "bf16val", 2)
+    assert sweep == pytest.approx(833e6, rel=0.01)
+
+
+def test_per_power_errors():
+    import numpy as np
+    import bench
+    ref = np.array([[1.0, -2.0], [0.0, 0.0]])
+    got = np.array([[1.0, -2.0 + 1e-3], [0.0, 1e-310]])
+    e = bench.per_power_errors(got, ref)
+    assert e[0] == pytest.approx(5e-4) and e[1] > 0

@@ -1,9 +1,11 @@
 """The allocation-free levels entry point (mpk_levels_noalloc), for callers
-that may not allocate device memory (for example inside a stream capture or
-under a fixed start-up memory budget).  It keeps its scratch in a static
-device array of the library; its output must equal the levels of the normal
-entry point (mpk_plan, read back with mpk_plan_perm) exactly, on two calls in
-a row (the second call reuses the array the first one left behind).
+that may not allocate device memory after start-up (a host that sizes all
+device memory once, under a fixed budget or a hard GPU quota).  It keeps its
+scratch in a static device array of the library; its output must equal the
+levels of the normal entry point (mpk_plan, read back with mpk_plan_perm)
+exactly, on two calls in a row (the second call reuses the array the first
+one left behind), and a call after a warm-up call must not change the
+device's free memory or the default memory pool's usage.
 
 This file is collected last on purpose."""
 import ctypes as C
@@ -16,6 +18,34 @@ import mpk_inputs as mi
 import paper_2205_01598_gb300 as mpk
 
 pytestmark = pytest.mark.gpu
+
+
+def _cudart():
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return C.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def _device_memory_state():
+    """(free device bytes, default pool's reserved bytes, default pool's used
+    bytes, torch's allocated bytes) on the current device."""
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    reserved = used = None
+    rt = _cudart()
+    if rt is not None:
+        dev = C.c_int()
+        pool = C.c_void_p()
+        if rt.cudaGetDevice(C.byref(dev)) == 0 and rt.cudaDeviceGetDefaultMemPool(C.byref(pool), dev) == 0:
+            r, u = C.c_uint64(), C.c_uint64()
+            if rt.cudaMemPoolGetAttribute(pool, 0x5, C.byref(r)) == 0:   # cudaMemPoolAttrReservedMemCurrent
+                reserved = r.value
+            if rt.cudaMemPoolGetAttribute(pool, 0x7, C.byref(u)) == 0:   # cudaMemPoolAttrUsedMemCurrent
+                used = u.value
+    return free, reserved, used, torch.cuda.memory_allocated()
 
 
 def _levels_noalloc(lib, rp, cl, root, out):
@@ -46,6 +76,25 @@ def test_noalloc_levels_equal_plan_levels_twice(make, root):
         assert rc == mpk.MPK_OK, mpk.mpk_strerror(rc)
         assert nl == ref_n
         assert torch.equal(out.cpu(), ref_levels)
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    mpk.build()
+    lib = mpk.load()
+    A = mi.laplace3d(60)
+    rp, cl, _ = mpk.csr_to_device(A)
+    out = torch.empty(A.n, dtype=torch.int32, device="cuda")
+    rc, nl = _levels_noalloc(lib, rp, cl, 0, out)          # warm-up: loads the kernels
+    assert rc == mpk.MPK_OK and nl == 3 * 59 + 1
+    before = _device_memory_state()
+    for _ in range(2):
+        rc, nl = _levels_noalloc(lib, rp, cl, 0, out)
+        assert rc == mpk.MPK_OK and nl == 3 * 59 + 1
+    assert _device_memory_state() == before
+    # the binding's wrapper passes the caller's output through unchanged
+    lev, nl2 = mpk.mpk_levels_noalloc(rp, cl, 0, out)
+    assert lev.data_ptr() == out.data_ptr() and nl2 == nl
+    assert _device_memory_state() == before
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch():
