@@ -296,78 +296,43 @@ __device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k
     return true;
 }
 
-// Bulk copy of the packed slice of work item wk (columns, then values) into
-// a shared-memory stage.  The L2 hint marks the slice evict-first at its last
-// power (no later reuse) and evict-last before (it is read again p-1 times).
+// Bytes of one shared-memory stage: the chunk records of a tile, then its
+// column indices, then its values, each part 128-byte aligned.
 template <typename MT>
-__device__ __forceinline__ void stage_item(const ExecArgs &a, int32_t wk, unsigned char *stage, uint64_t *mbar) {
-    const int32_t t = wk >> 8, k = wk & 255;
-    const int64_t o0 = __ldg(a.tile_off + t), o1 = __ldg(a.tile_off + t + 1);
-    const uint32_t ne = (uint32_t)(o1 - o0);
-    const uint64_t pol = k >= a.p ? l2_policy_evict_first()
-                                  : ((a.tune & MPK_TUNE_EVICT_LAST) ? l2_policy_evict_last() : l2_policy_evict_normal());
-    fence_proxy_async_smem();
-    mbar_expect_tx(mbar, ne * (uint32_t)(4 + sizeof(MT)));
-    bulk_g2s(stage, a.pcol + o0, ne * 4u, mbar, pol);
-    bulk_g2s(stage + (size_t)a.stage_entries * 4, (const MT *)a.pval + o0, ne * (uint32_t)sizeof(MT), mbar, pol);
+__device__ __forceinline__ size_t stage_bytes_of(const ExecArgs &a) {
+    return (((size_t)a.stage_recs * 16 + (size_t)a.stage_entries * (4 + sizeof(MT)) + 127) / 128) * 128;
 }
 
-// Single-vector rows of up to kCpw chunks of one warp with the matrix slice
-// in shared memory: the gathers of all chunks (kGb entries of each row per
-// pass) are issued before any of them is used, so that an item costs about
-// one gather round trip instead of one per chunk.
-constexpr int kCpw = 2;   // chunks of a warp handled together
-constexpr int kGb = 8;    // entries per row per pass
+// Bulk copy of tile t's packed slice -- chunk records, column indices,
+// values -- into a shared-memory stage (layout of stage_bytes_of), completing
+// on mbar.  Every part starts on a 128-byte boundary in global and shared
+// memory and is a multiple of 16 bytes long (chunks hold 32 entries).
+template <typename MT>
+__device__ __forceinline__ void stage_slice(const ExecArgs &a, int32_t t, unsigned char *stage, uint64_t *mbar,
+                                            int32_t *s_nch, int64_t *s_ebase, uint64_t pol) {
+    const int32_t c0 = __ldg(a.tile_chunk + t), c1 = __ldg(a.tile_chunk + t + 1);
+    const int64_t o0 = __ldg(a.tile_off + t), o1 = __ldg(a.tile_off + t + 1);
+    const uint32_t rb = (uint32_t)(c1 - c0) * 16u, cb = (uint32_t)(o1 - o0) * 4u,
+                   vb = (uint32_t)(o1 - o0) * (uint32_t)sizeof(MT);
+    *s_nch = c1 - c0;
+    *s_ebase = o0;
+    fence_proxy_async_smem();
+    mbar_expect_tx(mbar, rb + cb + vb);
+    unsigned char *cols = stage + (size_t)a.stage_recs * 16;
+    if (rb) bulk_g2s(stage, a.chunk_rec + c0, rb, mbar, pol);
+    if (cb) bulk_g2s(cols, a.pcol + o0, cb, mbar, pol);
+    if (vb) bulk_g2s(cols + (size_t)a.stage_entries * 4, (const MT *)a.pval + o0, vb, mbar, pol);
+}
 
-template <typename VT, typename MT, bool DIAG>
-__device__ __forceinline__ void warp_chunks_staged(const ExecArgs &a, const MatView<MT, true> &mv, int32_t c0,
-                                                   int32_t c1, int ncw, int lane, const VT *yin, VT *yout) {
-    for (int32_t cb = c0; cb < c1; cb += kCpw * ncw) {
-        int32_t row[kCpw], w[kCpw];
-        int64_t e0[kCpw];
-        int32_t wmax = 0;
-#pragma unroll
-        for (int i = 0; i < kCpw; i++) {
-            const int32_t c = cb + i * ncw;
-            row[i] = -1;
-            w[i] = 0;
-            e0[i] = 0;
-            if (c < c1) {
-                const int32_t r0 = __ldg(a.chunk_row + c);
-                const int64_t off = __ldg(a.chunk_off + c);
-                if (lane < __ldg(a.chunk_row + c + 1) - r0) {
-                    row[i] = a.row_map ? __ldg(a.row_map + r0 + lane) : r0 + lane;
-                    w[i] = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
-                    e0[i] = off + lane;
-                }
-            }
-            wmax = max(wmax, w[i]);
-        }
-        VT acc[kCpw];
-#pragma unroll
-        for (int i = 0; i < kCpw; i++) acc[i] = VT(0);
-        for (int32_t j0 = 0; j0 < wmax; j0 += kGb) {
-            VT g[kCpw][kGb];
-#pragma unroll
-            for (int i = 0; i < kCpw; i++)
-#pragma unroll
-                for (int u = 0; u < kGb; u++) {
-                    const int32_t col = j0 + u < w[i] ? mv.c(e0[i] + (int64_t)(j0 + u) * kChunk) : -1;
-                    g[i][u] = col >= 0 ? yin[col] : VT(0);
-                }
-#pragma unroll
-            for (int i = 0; i < kCpw; i++)
-#pragma unroll
-                for (int u = 0; u < kGb; u++)
-                    if (j0 + u < w[i]) acc[i] = fma(to_vt<MT, VT>(mv.v(e0[i] + (int64_t)(j0 + u) * kChunk)), g[i][u], acc[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < kCpw; i++) {
-            if (row[i] < 0) continue;
-            if (DIAG) acc[i] = fma((VT)__ldg(a.diag + row[i]), yin[row[i]], acc[i]);
-            yout[row[i]] = acc[i];
-        }
-    }
+// The slice of work item wk (tile, power): evict-first in L2 at its last
+// power (no later reuse), evict-normal (or evict-last when asked) before.
+template <typename MT>
+__device__ __forceinline__ void stage_item(const ExecArgs &a, int32_t wk, unsigned char *stage, uint64_t *mbar,
+                                           int32_t *s_nch, int64_t *s_ebase) {
+    const int32_t k = wk & 255;
+    const uint64_t pol = k >= a.p ? l2_policy_evict_first()
+                                  : ((a.tune & MPK_TUNE_EVICT_LAST) ? l2_policy_evict_last() : l2_policy_evict_normal());
+    stage_slice<MT>(a, wk >> 8, stage, mbar, s_nch, s_ebase, pol);
 }
 
 // ---------------------------------------------------------------- register-held slices
@@ -478,7 +443,8 @@ __device__ __forceinline__ void slice_sum(const ExecArgs &a, const Slice<MT, PC>
 // gathers of all their entries (kGb per row per pass) in flight together,
 // entries summed in stored order with padding skipped (as chunk_rows does, so
 // both round alike).  out(row, acc) writes a row.
-constexpr int kRC = 2;
+constexpr int kRC = 2;   // chunks of a warp handled together
+constexpr int kGb = 8;   // entries of a row per pass
 
 template <typename VT, typename MT, int G, typename Out>
 __device__ __forceinline__ void resident_rows(const ExecArgs &a, const int4 *srec, const int32_t *scol,
@@ -594,12 +560,8 @@ struct MpkNode {
         const VT *yin = k == 1 ? (const VT *)a.x : (const VT *)a.Y + (int64_t)(k - 2) * a.blk;
         VT *yout = (VT *)a.Y + (int64_t)(k - 1) * a.blk;
         const int32_t c1 = __ldg(a.tile_chunk + t + 1);
-        if constexpr (STAGED && W == 1 && EXACT) {
-            warp_chunks_staged<VT, MT, DIAG>(a, mv, __ldg(a.tile_chunk + t) + warp, c1, nwarps, lane, yin, yout);
-        } else {
-            for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps)
-                chunk_rows<VT, MT, W, EXACT, DIAG, STAGED, GB>(a, mv, c, lane, yin, yout);
-        }
+        for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps)
+            chunk_rows<VT, MT, W, EXACT, DIAG, STAGED, GB>(a, mv, c, lane, yin, yout);
     }
 };
 
@@ -659,14 +621,18 @@ template <typename Node, typename MT, bool STAGED, typename Src, typename Extra,
 __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, const Extra &extra) {
     extern __shared__ __align__(128) unsigned char dsmem[];
     __shared__ int s_item, s_stage, s_plan;
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[kMaxStages];
+    __shared__ int32_t s_nch[kMaxStages];
+    __shared__ int64_t s_ebase[kMaxStages];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ncw = (int)(blockDim.x >> 5) - 1;
     const int nthr = (int)blockDim.x;
-    const size_t stage_bytes = STAGED ? (size_t)g.stage_entries * (4 + sizeof(MT)) : 0;
+    // staged form: the i-th item of this CTA uses stage i mod nst, whose
+    // mbarrier completes its (i / nst)-th phase when the copy has landed
+    const int nst = STAGED ? g.n_stages : 1;
+    const size_t stage_bytes = STAGED ? stage_bytes_of<MT>(g) : 0;
     if (STAGED && threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int q = 0; q < nst; q++) mbar_init(&mbar[q], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -674,12 +640,14 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
     if (warp == ncw) {
         // ------------------------------------------------------------ scheduler warp
         const int G = (int)gridDim.x;
-        int32_t issued[2] = {0, 0}, consumed[2] = {0, 0};   // bulk copies per stage
-        auto issue = [&](int32_t jj, int st) {
+        int32_t issued = 0, consumed = 0;   // bulk copies issued / items finished (staged form)
+        auto issue = [&](int32_t jj) {      // the next copy goes to stage issued mod nst
             if (STAGED) {
+                const int st = issued % nst;
                 if (lane == 0)
-                    stage_item<MT>(src.args(src.plan_of(jj)), __ldg(g.work + jj), dsmem + st * stage_bytes, &mbar[st]);
-                issued[st]++;
+                    stage_item<MT>(src.args(src.plan_of(jj)), __ldg(g.work + jj), dsmem + st * stage_bytes, &mbar[st],
+                                   &s_nch[st], &s_ebase[st]);
+                issued++;
             }
         };
         FlagProbe pr;
@@ -687,8 +655,8 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
         bool ok = j < g.n_items;
         int32_t m = 0;
         if (ok) {
-            issue(j, 0);
-            if (j + G < g.n_items) issue(j + G, 1);
+            for (int q = 0; q < nst; q++)
+                if (j + q * G < g.n_items) issue(j + q * G);
             const int32_t wk = __ldg(g.work + j);
             m = src.plan_of(j);
             if ((wk & 255) > 1) {
@@ -721,7 +689,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
         // the one read from HBM (later powers find it in L2); its bulk
         // prefetch into L2 is issued four items ahead, after two steps of
         // loads (work word, then slice range) spread over the items before.
-        constexpr bool kL2Ahead = Node::kL2First;
+        constexpr bool kL2Ahead = Node::kL2First && !STAGED;
         int32_t pfw = -1, pfmw = 0;   // item j + 5G: work word (-1 none) and plan
         int64_t pfo0 = 0, pfo1 = 0;   // item j + 4G: packed entries, when a power-1 item
         int32_t pfm = 0;
@@ -770,7 +738,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
                 }
             }
             named_sync(kBarDone, nthr);   // compute warps finished item j
-            if (STAGED) consumed[i & 1]++;
+            if (STAGED) consumed++;
             auto publish = [&]() {
                 const ExecArgs &aj = src.args(m);
                 const int32_t t = wk >> 8, k = wk & 255;
@@ -788,11 +756,11 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
                 publish();
                 ready = wait_deps(src.args(mn), pr, wn >> 8, wn & 255, src.epoch_of(mn), lane);
             }
-            if (ready && j + 2 * G < g.n_items) issue(j + 2 * G, i & 1);   // stage of item j is free
+            if (ready && j + nst * G < g.n_items) issue(j + nst * G);   // the stage of item j is free
             if (lane == 0) {
                 s_item = ready ? wn : -1;
                 s_plan = mn;
-                s_stage = (i + 1) & 1;
+                s_stage = (i + 1) % nst;
             }
             __syncwarp();
             named_arrive(kBarReady, nthr);
@@ -802,13 +770,11 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             m = mn;
             i++;
         }
-        // never leave with a bulk copy in flight (abort path)
-        for (int st = 0; STAGED && st < 2; st++)
-            while (consumed[st] < issued[st]) {
-                if (!mbar_wait(&mbar[st], (uint32_t)(consumed[st] & 1), g.timeout_ns) && lane == 0)
-                    record_timeout(g, 0, -1);
-                consumed[st]++;
-            }
+        // never leave with a bulk copy in flight (abort path): copy q went to
+        // stage q mod nst and completes that mbarrier's (q / nst)-th phase
+        for (int32_t q = consumed; STAGED && q < issued; q++)
+            if (!mbar_wait(&mbar[q % nst], (uint32_t)((q / nst) & 1), g.timeout_ns) && lane == 0)
+                record_timeout(g, 0, -1);
         __syncwarp();
         if (lane == 0) {
             __threadfence();
@@ -858,31 +824,40 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             j += G;
             named_arrive(kBarDone, nthr);
         }
-    } else {
-        // ------------------------------------------------------------ compute warps
-        uint32_t ph0 = 0, ph1 = 0;
-        for (;;) {
+    } else if constexpr (STAGED) {
+        // ------------------------------------------------------------ compute warps, staged slices
+        // The item's chunk records, indices and values are in its stage, so
+        // the first global access of an item is the gather of its inputs.
+        const size_t rec_bytes = (size_t)g.stage_recs * 16;
+        for (int32_t i = 0;; i++) {
             named_sync(kBarReady, nthr);
             const int32_t wk = *(volatile int *)&s_item;
             const int st = *(volatile int *)&s_stage;
             const int32_t m = *(volatile int *)&s_plan;
             if (wk < 0) break;
+            const ExecArgs &a = src.args(m);
+            if (!mbar_wait(&mbar[st], (uint32_t)((i / nst) & 1), g.timeout_ns)) {
+                if (lane == 0) record_timeout(g, wk & 255, wk >> 8);
+                named_arrive(kBarDone, nthr);
+                continue;
+            }
+            const unsigned char *sb = dsmem + st * stage_bytes;
+            Node::res_run(a, (const int4 *)sb, (const int32_t *)(sb + rec_bytes),
+                          (const MT *)(sb + rec_bytes + (size_t)g.stage_entries * 4), s_ebase[st], s_nch[st],
+                          wk & 255, warp, ncw, lane, extra);
+            named_arrive(kBarDone, nthr);
+        }
+    } else {
+        // ------------------------------------------------------------ compute warps
+        for (;;) {
+            named_sync(kBarReady, nthr);
+            const int32_t wk = *(volatile int *)&s_item;
+            const int32_t m = *(volatile int *)&s_plan;
+            if (wk < 0) break;
             const int32_t t = wk >> 8, k = wk & 255;
             const ExecArgs &a = src.args(m);
-            if (STAGED) {
-                const bool landed = mbar_wait(&mbar[st], st ? ph1 : ph0, g.timeout_ns);
-                if (st) ph1 ^= 1u; else ph0 ^= 1u;
-                if (!landed) {
-                    if (lane == 0) record_timeout(g, k, t);
-                    named_arrive(kBarDone, nthr);
-                    continue;
-                }
-            }
-            const MatView<MT, STAGED> mv{STAGED ? (const int32_t *)(dsmem + st * stage_bytes) : a.pcol,
-                                         STAGED ? (const MT *)(dsmem + st * stage_bytes + (size_t)g.stage_entries * 4)
-                                                : (const MT *)a.pval,
-                                         STAGED ? __ldg(a.tile_off + t) : 0};
-            Node::template run<STAGED>(a, mv, t, k, warp, ncw, lane, extra);
+            const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
+            Node::template run<false>(a, mv, t, k, warp, ncw, lane, extra);
             named_arrive(kBarDone, nthr);
         }
     }
@@ -908,19 +883,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
 template <typename MT>
 __device__ __forceinline__ void stage_tile(const ExecArgs &a, int32_t t, unsigned char *stage, uint64_t *mbar,
                                            int32_t *s_nch, int64_t *s_ebase) {
-    const int32_t c0 = __ldg(a.tile_chunk + t), c1 = __ldg(a.tile_chunk + t + 1);
-    const int64_t o0 = __ldg(a.tile_off + t), o1 = __ldg(a.tile_off + t + 1);
-    const uint32_t rb = (uint32_t)(c1 - c0) * 16u, cb = (uint32_t)(o1 - o0) * 4u,
-                   vb = (uint32_t)(o1 - o0) * (uint32_t)sizeof(MT);
-    *s_nch = c1 - c0;
-    *s_ebase = o0;
-    const uint64_t pol = l2_policy_evict_first();   // read once per sweep
-    fence_proxy_async_smem();
-    mbar_expect_tx(mbar, rb + cb + vb);
-    unsigned char *cols = stage + (size_t)a.stage_recs * 16;
-    if (rb) bulk_g2s(stage, a.chunk_rec + c0, rb, mbar, pol);
-    if (cb) bulk_g2s(cols, a.pcol + o0, cb, mbar, pol);
-    if (vb) bulk_g2s(cols + (size_t)a.stage_entries * 4, (const MT *)a.pval + o0, vb, mbar, pol);
+    stage_slice<MT>(a, t, stage, mbar, s_nch, s_ebase, l2_policy_evict_first());   // read once per sweep
 }
 
 template <typename Node, typename MT, typename Extra>
@@ -934,7 +897,7 @@ __device__ __forceinline__ void resident_loop(const ExecArgs &a, uint32_t epoch,
     const int ncw = (int)(blockDim.x >> 5) - 1;
     const int nthr = (int)blockDim.x;
     const size_t rec_bytes = (size_t)a.stage_recs * 16;
-    const size_t stage_bytes = ((rec_bytes + (size_t)a.stage_entries * (4 + sizeof(MT)) + 127) / 128) * 128;
+    const size_t stage_bytes = stage_bytes_of<MT>(a);
     const int32_t P = a.p;
     const int32_t G = (int32_t)gridDim.x;
     if (threadIdx.x == 0) {
@@ -1089,91 +1052,176 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(ExecArgs a, const VT *yin
         chunk_rows<VT, MT, W, EXACT, DIAG, false>(a, mv, (int32_t)c, lane, yin, yout);
 }
 
+// ---------------------------------------------------------------- double-float arithmetic
+// A double-float value is the unevaluated sum hi + lo of two FP32 numbers.
+// Sums are split exactly by Knuth's branch-free TwoSum, products by the FMA
+// form of Dekker's product (p = a b, e = fma(a, b, -p) is the exact
+// rounding error); FP32's 24-bit significand gives pairs of about 48
+// significant bits.  GB300 runs FP32 at about 60 times its FP64 rate, so
+// the parts of the Chebyshev node that need more than FP32 run in pairs.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+// acc = (hi, lo) += (ch + cl) * v: the exact product ch*v, the small cl*v,
+// and a TwoSum whose error goes to lo (one step of the compensated dot
+// product of Ogita, Rump and Oishi, Dot2).  Terms are added one at a time in
+// a fixed order, so the result does not depend on where acc is kept between
+// terms.
+__device__ __forceinline__ void dot2_add(float &hi, float &lo, float ch, float cl, float v) {
+    float p, r, s, q;
+    two_prod(ch, v, p, r);
+    r = fmaf(cl, v, r);
+    two_sum(hi, p, s, q);
+    hi = s;
+    lo += q + r;
+}
+
 // ---------------------------------------------------------------- Chebyshev
-// Node of a sweep: global power k = k0 + j.  With Ahat = (A - c)/r:
+// Node of a sweep: global power k = k0 + j, j = 1..pw.  With Ahat = (A - c)/r:
 //   v_1 = Ahat v_0,  v_k = 2 Ahat v_{k-1} - v_{k-2},  acc += coef_k v_k,
 // vectors in a ring of three blocks, G columns: G = 2 complex (re, im; the
 // Schroedinger propagator, complex coefficients), G = 1 real (the heat
-// propagator, real coefficients).  A v is summed in the storage precision;
-// the scaling, the recurrence update and the coefficient sum are done in FP64.
+// propagator, real coefficients).  A v is summed in the storage precision.
+// FP64 plans do the rest in FP64.  FP32 plans do the spectral scaling in
+// double-float (the diagonal shift d - c exactly, then 1/r), round once to
+// FP32 at the recurrence, and keep the coefficient sum in double-float.
+//
+// The coefficient sum is read and written every third power of a sweep and
+// at its last power: the node of power k holds v_{k-2}, v_{k-1} (its own
+// row of the two input vectors) and v_k, so it adds the terms not yet added
+// (local powers 3q+1 .. j) in ascending k.  The terms and their order are
+// the same however M is split into sweeps, so every split gives the same
+// bits.
 template <typename VT, typename MT, bool DIAG, int G>
 struct ChebNode {
     static constexpr bool kL2First = false;
     static_assert(G == 1 || G == 2, "real or complex vectors");
     static constexpr bool kPipe = true;
+    static constexpr bool kF64 = sizeof(VT) == 8;
 
     struct Vecs {
         const VT *yin, *yprev;
         VT *yout;
-        double cre, cim;
-        int32_t k;
+        int32_t k;       // global power
+        int32_t nterm;   // coefficient terms this node adds (0: none, else 1..3 ending at k)
     };
     __device__ __forceinline__ static Vecs vecs(const ExecArgs &a, const ChebArgs &ca, int32_t j) {
         const int32_t k = ca.k0 + j;
         VT *ring = (VT *)ca.ring;
+        const int32_t flush = (j % 3 == 0 || j == ca.pw) ? j - 3 * ((j - 1) / 3) : 0;
         return Vecs{ring + (int64_t)((k - 1) % 3) * a.blk, ring + (int64_t)((k + 1) % 3) * a.blk,   // (k-2) mod 3
-                    ring + (int64_t)(k % 3) * a.blk, G == 2 ? ca.coef[2 * k] : ca.coef[k],
-                    G == 2 ? ca.coef[2 * k + 1] : 0.0, k};
+                    ring + (int64_t)(k % 3) * a.blk, k, flush};
     }
 
-    // Row r of the sweep step, given s = (A v_{k-1})[r] without a separately
-    // stored diagonal.
-    // complex state, written out for two columns (this form schedules better
-    // than the loop over columns below)
-    __device__ __forceinline__ static void row_out2(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
-                                                    VT s0, VT s1) {
-        const double u0 = (double)v.yin[2 * (int64_t)r], u1 = (double)v.yin[2 * (int64_t)r + 1];
-        double a0, a1;
-        if (DIAG) {   // the diagonal term enters in FP64 together with the shift
-            const double d = (double)__ldg(a.diag + r);
-            a0 = ca.alpha * ((double)s0 + d * u0) + ca.beta * u0;
-            a1 = ca.alpha * ((double)s1 + d * u1) + ca.beta * u1;
-        } else {
-            a0 = ca.alpha * (double)s0 + ca.beta * u0;
-            a1 = ca.alpha * (double)s1 + ca.beta * u1;
-        }
-        double n0 = a0, n1 = a1;
-        if (v.k > 1) {
-            n0 = 2.0 * a0 - (double)v.yprev[2 * (int64_t)r];
-            n1 = 2.0 * a1 - (double)v.yprev[2 * (int64_t)r + 1];
-        }
-        v.yout[2 * (int64_t)r] = (VT)n0;
-        v.yout[2 * (int64_t)r + 1] = (VT)n1;
-        double *acc = ca.acc + 2 * (int64_t)r;
-        acc[0] += v.cre * n0 - v.cim * n1;
-        acc[1] += v.cre * n1 + v.cim * n0;
-    }
-
+    // Row r of the node, given s = the row's sum of value * v_{k-1} over its
+    // stored entries (without the diagonal when it is stored apart).  Every
+    // load comes before the first store: the ring blocks may alias as far as
+    // the compiler knows, and a load behind a store waits for it.
     __device__ __forceinline__ static void row_out(const ExecArgs &a, const ChebArgs &ca, const Vecs &v, int32_t r,
                                                    const VT (&s)[G]) {
-        if constexpr (G == 2) {
-            row_out2(a, ca, v, r, s[0], s[G - 1]);
-            return;
-        }
-        // every load before the first store: the ring blocks may alias as far
-        // as the compiler knows, and a load behind a store waits for it
-        double u[G], pv[G], nv[G];
-        const double d = DIAG ? (double)__ldg(a.diag + r) : 0.0;
+        VT u[G], pv[G], nv[G];
 #pragma unroll
         for (int q = 0; q < G; q++) {
-            u[q] = (double)v.yin[G * (int64_t)r + q];
-            pv[q] = v.k > 1 ? (double)v.yprev[G * (int64_t)r + q] : 0.0;
+            u[q] = v.yin[G * (int64_t)r + q];
+            pv[q] = v.k > 1 ? v.yprev[G * (int64_t)r + q] : VT(0);
         }
+        if constexpr (kF64) {
+            double *acc = (double *)ca.acc + G * (int64_t)r;
+            double ac[G];
+            if (v.nterm) {
 #pragma unroll
-        for (int q = 0; q < G; q++) {
-            // the diagonal term enters in FP64 together with the shift
-            const double ah = DIAG ? ca.alpha * ((double)s[q] + d * u[q]) + ca.beta * u[q]
-                                   : ca.alpha * (double)s[q] + ca.beta * u[q];
-            nv[q] = v.k > 1 ? 2.0 * ah - pv[q] : ah;
-        }
+                for (int q = 0; q < G; q++) ac[q] = acc[q];
+            }
 #pragma unroll
-        for (int q = 0; q < G; q++) v.yout[G * (int64_t)r + q] = (VT)nv[q];
-        double *acc = ca.acc + G * (int64_t)r;
-        if (G == 2) {
-            acc[0] += v.cre * nv[0] - v.cim * nv[G - 1];
-            acc[G - 1] += v.cre * nv[G - 1] + v.cim * nv[0];
+            for (int q = 0; q < G; q++) {
+                const double ah = ca.alpha * (double)s[q] + ca.beta * (double)u[q];
+                nv[q] = v.k > 1 ? 2.0 * ah - (double)pv[q] : ah;
+            }
+#pragma unroll
+            for (int q = 0; q < G; q++) v.yout[G * (int64_t)r + q] = nv[q];
+            if (v.nterm) {
+                auto add = [&](const VT (&t)[G], int32_t kt) {
+                    if constexpr (G == 2) {
+                        const double cre = ca.coef[2 * kt], cim = ca.coef[2 * kt + 1];
+                        ac[0] = fma(cre, (double)t[0], fma(-cim, (double)t[1], ac[0]));
+                        ac[1] = fma(cre, (double)t[1], fma(cim, (double)t[0], ac[1]));
+                    } else {
+                        ac[0] = fma(ca.coef[kt], (double)t[0], ac[0]);
+                    }
+                };
+                if (v.nterm >= 3) add(pv, v.k - 2);
+                if (v.nterm >= 2) add(u, v.k - 1);
+                add(nv, v.k);
+#pragma unroll
+                for (int q = 0; q < G; q++) acc[q] = ac[q];
+            }
         } else {
-            acc[0] += v.cre * nv[0];
+            float *acc = (float *)ca.acc + 2 * G * (int64_t)r;   // (hi, lo) per column
+            float ac[2 * G];
+            if (v.nterm) {
+                if constexpr (G == 2) {
+                    const float4 t = *reinterpret_cast<const float4 *>(acc);
+                    ac[0] = t.x, ac[1] = t.y, ac[2] = t.z, ac[3] = t.w;
+                } else {
+                    const float2 t = *reinterpret_cast<const float2 *>(acc);
+                    ac[0] = t.x, ac[1] = t.y;
+                }
+            }
+            float dh = 0.f, dl = 0.f;
+            if (DIAG) {   // d - c, exactly up to the rounding of c's low part
+                two_sum((float)__ldg(a.diag + r), -ca.c_hi, dh, dl);
+                dl -= ca.c_lo;
+            }
+#pragma unroll
+            for (int q = 0; q < G; q++) {
+                float h, l;
+                if (DIAG) {   // Ahat v = (s + (d - c) u) / r
+                    float p, pe, wh, wl;
+                    two_prod(dh, (float)u[q], p, pe);
+                    pe = fmaf(dl, (float)u[q], pe);
+                    two_sum((float)s[q], p, wh, wl);
+                    wl += pe;
+                    two_prod(ca.alpha_hi, wh, h, l);
+                    l = fmaf(ca.alpha_hi, wl, fmaf(ca.alpha_lo, wh, l));
+                } else {      // Ahat v = s / r - (c / r) u
+                    float h1, l1, h2, l2;
+                    two_prod(ca.alpha_hi, (float)s[q], h1, l1);
+                    l1 = fmaf(ca.alpha_lo, (float)s[q], l1);
+                    two_prod(ca.beta_hi, (float)u[q], h2, l2);
+                    l2 = fmaf(ca.beta_lo, (float)u[q], l2);
+                    two_sum(h1, h2, h, l);
+                    l += l1 + l2;
+                }
+                nv[q] = v.k > 1 ? fmaf(2.f, h, -(float)pv[q]) + 2.f * l : h + l;
+            }
+#pragma unroll
+            for (int q = 0; q < G; q++) v.yout[G * (int64_t)r + q] = nv[q];
+            if (v.nterm) {
+                auto add = [&](const VT (&t)[G], int32_t kt) {
+                    const float4 c = __ldg(ca.coef_df + kt);
+                    if constexpr (G == 2) {   // (c_re + i c_im)(t_re + i t_im)
+                        dot2_add(ac[0], ac[1], c.x, c.y, (float)t[0]);
+                        dot2_add(ac[0], ac[1], -c.z, -c.w, (float)t[1]);
+                        dot2_add(ac[2], ac[3], c.x, c.y, (float)t[1]);
+                        dot2_add(ac[2], ac[3], c.z, c.w, (float)t[0]);
+                    } else {
+                        dot2_add(ac[0], ac[1], c.x, c.y, (float)t[0]);
+                    }
+                };
+                if (v.nterm >= 3) add(pv, v.k - 2);
+                if (v.nterm >= 2) add(u, v.k - 1);
+                add(nv, v.k);
+                if constexpr (G == 2)
+                    *reinterpret_cast<float4 *>(acc) = make_float4(ac[0], ac[1], ac[2], ac[3]);
+                else
+                    *reinterpret_cast<float2 *>(acc) = make_float2(ac[0], ac[1]);
+            }
         }
     }
 
@@ -1187,29 +1235,6 @@ struct ChebNode {
         const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
         const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
         const int64_t e0 = off + lane;
-        if constexpr (G == 2) {   // complex state: two scalar sums
-            VT s0 = VT(0), s1 = VT(0);
-            constexpr int B = 8;
-            for (int32_t q0 = 0; q0 < w; q0 += B) {
-                int32_t cols[B];
-                VT vals[B];
-#pragma unroll
-                for (int u = 0; u < B; u++) {
-                    const bool in = q0 + u < w;
-                    cols[u] = in ? mv.c(e0 + (int64_t)(q0 + u) * kChunk) : -1;
-                    vals[u] = in ? to_vt<MT, VT>(mv.v(e0 + (int64_t)(q0 + u) * kChunk)) : VT(0);
-                }
-#pragma unroll
-                for (int u = 0; u < B; u++) {
-                    if (cols[u] >= 0) {
-                        s0 = fma(vals[u], v.yin[2 * (int64_t)cols[u]], s0);
-                        s1 = fma(vals[u], v.yin[2 * (int64_t)cols[u] + 1], s1);
-                    }
-                }
-            }
-            row_out2(a, ca, v, r, s0, s1);
-            return;
-        }
         VT sum[G];
 #pragma unroll
         for (int q = 0; q < G; q++) sum[q] = VT(0);
@@ -1255,11 +1280,8 @@ struct ChebNode {
         VT acc[PC][G];
         slice_sum<VT, MT, G, PC>(a, s, v.yin, lane, acc);
 #pragma unroll
-        for (int i = 0; i < PC; i++) {
-            if (s.row[i] < 0) continue;
-            if constexpr (G == 2) row_out2(a, ca, v, s.row[i], acc[i][0], acc[i][G - 1]);
-            else row_out(a, ca, v, s.row[i], acc[i]);
-        }
+        for (int i = 0; i < PC; i++)
+            if (s.row[i] >= 0) row_out(a, ca, v, s.row[i], acc[i]);
         const MatView<MT, false> mv{a.pcol, (const MT *)a.pval, 0};
         for (int32_t c = s.c0 + warp + PC * nwarps; c < s.c1; c += nwarps) chunk<false>(a, mv, c, lane, ca, v);
     }
@@ -1322,17 +1344,56 @@ __global__ void __launch_bounds__(kWaveThreads, MPK_BATCH_MIN_BLOCKS) k_batch_wa
     wave_loop<BatchNode<VT, MT>, MT, false>(b.g, src, 0);
 }
 
-// acc = coef_0 * v_0 (complex for G = 2, real for G = 1), v_0 = ring block 0
-template <typename VT, int G>
-__global__ void k_cheb_init(int32_t n, const VT *v0, const double *coef, double *acc) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// acc = coef_0 * v_0 (complex for G = 2, real for G = 1), v_0 = ring block 0:
+// FP64 for FP64 plans, double-float pairs (the node's arithmetic, from zero)
+// for FP32 plans.
+template <int G>
+__global__ void k_cheb_init_f64(int32_t n, const double *v0, const double *coef, double *acc) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     if (G == 2) {
-        const double x0 = (double)v0[2 * r], x1 = (double)v0[2 * r + 1];
-        acc[2 * r] = coef[0] * x0 - coef[1] * x1;
-        acc[2 * r + 1] = coef[0] * x1 + coef[1] * x0;
+        const double x0 = v0[2 * r], x1 = v0[2 * r + 1];
+        acc[2 * r] = fma(coef[0], x0, fma(-coef[1], x1, 0.0));
+        acc[2 * r + 1] = fma(coef[0], x1, fma(coef[1], x0, 0.0));
     } else {
-        acc[r] = coef[0] * (double)v0[r];
+        acc[r] = fma(coef[0], v0[r], 0.0);
+    }
+}
+template <int G>
+__global__ void k_cheb_init_df(int32_t n, const float *v0, const float4 *coef_df, float *acc) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float4 c = coef_df[0];
+    if (G == 2) {
+        const float x0 = v0[2 * r], x1 = v0[2 * r + 1];
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+        dot2_add(a[0], a[1], c.x, c.y, x0);
+        dot2_add(a[0], a[1], -c.z, -c.w, x1);
+        dot2_add(a[2], a[3], c.x, c.y, x1);
+        dot2_add(a[2], a[3], c.z, c.w, x0);
+        reinterpret_cast<float4 *>(acc)[r] = make_float4(a[0], a[1], a[2], a[3]);
+    } else {
+        float a[2] = {0.f, 0.f};
+        dot2_add(a[0], a[1], c.x, c.y, v0[r]);
+        reinterpret_cast<float2 *>(acc)[r] = make_float2(a[0], a[1]);
+    }
+}
+
+// y[r] = hi + lo in FP64 for each column of row idx[r] (idx = NULL: row r)
+// of a double-float sum.  With idx = NULL, y may be the sum itself (each row's
+// 8G bytes are read, then written, by the same thread).
+template <int G>
+__global__ void k_cheb_df_to_f64(int32_t n, const float *acc, const int32_t *__restrict__ idx, double *y) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t from = idx ? (int64_t)__ldg(idx + r) : r;
+        if (G == 2) {
+            const float4 t = reinterpret_cast<const float4 *>(acc)[from];
+            const double2 o = make_double2((double)t.x + (double)t.y, (double)t.z + (double)t.w);
+            reinterpret_cast<double2 *>(y)[r] = o;
+        } else {
+            const float2 t = reinterpret_cast<const float2 *>(acc)[from];
+            y[r] = (double)t.x + (double)t.y;
+        }
     }
 }
 
@@ -1410,13 +1471,24 @@ const void *spmv_ptr(int nrhs) {
     }
 }
 
+template <typename VT, typename MT, bool DIAG, int NW>
+const void *staged_wave_ptr(int nrhs) {   // the staged form runs block widths 1 and 2
+    return nrhs == 1 ? (const void *)k_wave<VT, MT, 1, true, DIAG, true, NW>
+                     : (const void *)k_wave<VT, MT, 2, true, DIAG, true, NW>;
+}
 template <bool STAGED>
 const void *pick_wave_t(const Plan *pl) {
-    if (pl->prec == MPK_F64) return wave_ptr<double, double, false, STAGED, STAGED ? kComputeWarps : kFp64Warps>(pl->nrhs);
-    constexpr int NW = STAGED ? kComputeWarps : kFp32Warps;
-    if (!pl->has_diag) return wave_ptr<float, float, false, STAGED, NW>(pl->nrhs);
-    if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, STAGED, NW>(pl->nrhs);
-    return wave_ptr<float, float, true, STAGED, NW>(pl->nrhs);
+    if constexpr (STAGED) {
+        if (pl->prec == MPK_F64) return staged_wave_ptr<double, double, false, kFp64Warps>(pl->nrhs);
+        if (!pl->has_diag) return staged_wave_ptr<float, float, false, kFp32Warps>(pl->nrhs);
+        if (pl->val_bytes == 2) return staged_wave_ptr<float, __nv_bfloat16, true, kFp32Warps>(pl->nrhs);
+        return staged_wave_ptr<float, float, true, kFp32Warps>(pl->nrhs);
+    } else {
+        if (pl->prec == MPK_F64) return wave_ptr<double, double, false, false, kFp64Warps>(pl->nrhs);
+        if (!pl->has_diag) return wave_ptr<float, float, false, false, kFp32Warps>(pl->nrhs);
+        if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, false, kFp32Warps>(pl->nrhs);
+        return wave_ptr<float, float, true, false, kFp32Warps>(pl->nrhs);
+    }
 }
 template <bool STAGED, int G>
 const void *pick_cheb_g(const Plan *pl) {
@@ -1519,6 +1591,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.stage_recs = pl->stage_recs;
     a.stage_entries = pl->stage_entries;
     a.tune = pl->tune;
+    a.n_stages = pl->n_stages;
     return a;
 }
 
@@ -1759,6 +1832,13 @@ int mpk_gershgorin(mpk_plan_t plan, double *lo, double *hi) {
     return MPK_OK;
 }
 
+// Splits x into FP32 hi + lo with hi = x rounded to FP32 (exact pairs for
+// the double-float node).
+static inline void split_f64(double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
 // Chebyshev propagation with G vector columns (2: complex state and
 // coefficients, 1: real); the plan's block width must be G.
 static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
@@ -1768,11 +1848,33 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
     if (pl->nrhs != G) return MPK_ERR_INVALID;
     cudaStream_t st = pl->stream;
     const int eb = elem_bytes_of(pl);
+    const bool df = eb == 4;   // FP32 vectors: double-float scaling and coefficient sum
     const size_t blk = (size_t)pl->n * G;
-    // device storage: 3-block ring (storage precision), FP64 accumulator, coefficients
+    std::vector<float4> cdf;
+    ChebArgs ca;
+    ca.alpha = 1.0 / r;
+    ca.beta = -c / r;
+    if (df) {
+        // the pairs must stay inside FP32's range
+        const double lim = 1e30;
+        if (!(std::fabs(ca.alpha) <= lim && std::fabs(ca.beta) <= lim && std::fabs(c) <= lim)) return MPK_ERR_UNSUPPORTED;
+        cdf.resize((size_t)M + 1);
+        for (int32_t k = 0; k <= M; k++) {
+            const double re = coef[(size_t)G * k], im = G == 2 ? coef[(size_t)G * k + 1] : 0.0;
+            if (!(std::fabs(re) <= lim && std::fabs(im) <= lim)) return MPK_ERR_UNSUPPORTED;
+            split_f64(re, cdf[k].x, cdf[k].y);
+            split_f64(im, cdf[k].z, cdf[k].w);
+        }
+        split_f64(ca.alpha, ca.alpha_hi, ca.alpha_lo);
+        split_f64(ca.beta, ca.beta_hi, ca.beta_lo);
+        split_f64(c, ca.c_hi, ca.c_lo);
+    }
+    // device storage: 3-block ring (storage precision), the coefficient sum
+    // (FP64, or double-float pairs of the same size) unless it lives in y,
+    // and the coefficients (FP64 and double-float tables)
     const size_t ring_b = 3 * blk * eb, acc_b = (flags & MPK_IO_PERMUTED) ? 0 : blk * sizeof(double);
-    const size_t coef_b = sizeof(double) * G * ((size_t)M + 1);
-    const size_t need = ring_b + acc_b + coef_b + 256;
+    const size_t coef_b = sizeof(double) * G * ((size_t)M + 1), coefdf_b = sizeof(float4) * ((size_t)M + 1);
+    const size_t need = ring_b + acc_b + coef_b + coefdf_b + 256;
     if (pl->cheb_bytes < need) {
         if (pl->d_cheb) {
             cudaStreamSynchronize(st);
@@ -1788,9 +1890,11 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
     }
     char *base = (char *)pl->d_cheb;
     void *ring = base;
-    double *acc = (flags & MPK_IO_PERMUTED) ? y : (double *)(base + ring_b);
+    void *acc = (flags & MPK_IO_PERMUTED) ? (void *)y : (void *)(base + ring_b);
     double *dcoef = (double *)(base + ring_b + acc_b);
+    float4 *dcoef_df = (float4 *)(((uintptr_t)(base + ring_b + acc_b + coef_b) + 15) & ~(uintptr_t)15);
     MPK_CUDA(cudaMemcpyAsync(dcoef, coef, coef_b, cudaMemcpyHostToDevice, st));
+    if (df) MPK_CUDA(cudaMemcpyAsync(dcoef_df, cdf.data(), coefdf_b, cudaMemcpyHostToDevice, st));
     int rc;
     if (flags & MPK_IO_PERMUTED) {
         MPK_CUDA(cudaMemcpyAsync(ring, x, blk * eb, cudaMemcpyDeviceToDevice, st));
@@ -1799,19 +1903,17 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
     }
     const unsigned nb = (unsigned)((pl->n + 255) / 256);
     if (G == 2) {
-        if (eb == 8) k_cheb_init<double, 2><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, acc);
-        else k_cheb_init<float, 2><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef, acc);
+        if (!df) k_cheb_init_f64<2><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, (double *)acc);
+        else k_cheb_init_df<2><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef_df, (float *)acc);
     } else {
-        if (eb == 8) k_cheb_init<double, 1><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, acc);
-        else k_cheb_init<float, 1><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef, acc);
+        if (!df) k_cheb_init_f64<1><<<nb, 256, 0, st>>>(pl->n, (const double *)ring, dcoef, (double *)acc);
+        else k_cheb_init_df<1><<<nb, 256, 0, st>>>(pl->n, (const float *)ring, dcoef_df, (float *)acc);
     }
     MPK_CUDA(cudaGetLastError());
-    ChebArgs ca;
     ca.ring = ring;
     ca.acc = acc;
     ca.coef = dcoef;
-    ca.alpha = 1.0 / r;
-    ca.beta = -c / r;
+    ca.coef_df = dcoef_df;
     const int32_t sweep = (flags & MPK_SWEEP_ONE) ? 1 : pl->p;
     for (int32_t k0 = 0; k0 < M; k0 += sweep) {
         const int32_t pw = std::min(sweep, M - k0);
@@ -1836,10 +1938,18 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
             ca.e.p = pw;
         }
         ca.k0 = k0;
+        ca.pw = pw;
         void *args[] = {(void *)&ca};
         if ((rc = launch_coop(pick_cheb(pl), pl->cheb_grid, pl->smem_bytes, args, st, cheb_threads(pl)))) return rc;
     }
-    if (!(flags & MPK_IO_PERMUTED)) {
+    if (df) {
+        // double-float sum -> FP64 y (in place in level order, else gathered
+        // into the caller's numbering)
+        const int32_t *idx = (flags & MPK_IO_PERMUTED) ? nullptr : pl->d_iperm;
+        const unsigned g = (unsigned)std::min<int64_t>(((int64_t)pl->n + 255) / 256, (int64_t)pl->num_sms * 8);
+        if (G == 2) k_cheb_df_to_f64<2><<<g, 256, 0, st>>>(pl->n, (const float *)acc, idx, y);
+        else k_cheb_df_to_f64<1><<<g, 256, 0, st>>>(pl->n, (const float *)acc, idx, y);
+    } else if (!(flags & MPK_IO_PERMUTED)) {
         // acc (level order, n x G doubles) -> y (original order)
         if ((rc = permute_vectors(pl, acc, y, 1, 8, 0, st))) return rc;
     }

@@ -32,6 +32,7 @@ constexpr int kSpmvThreads = 256;                        // baseline SpMV CTA
 #endif
 constexpr int kResWarps = MPK_RES_WARPS;                 // compute warps of a resident-schedule CTA
 constexpr int kResThreads = (kResWarps + 1) * 32;
+constexpr int kMaxStages = 3;                            // shared-memory stages of the staged work-list form
 
 // Control words of a plan (device int32 array).
 enum Ctl : int {
@@ -65,6 +66,7 @@ struct Plan {
     int32_t drop_tile = -1, drop_k = -1;   // one-shot test hook (mpk_plan_debug_drop_flag)
     uint32_t tune = 0;              // MPK_TUNE_* bits
     int32_t staged = 0;             // matrix slices staged in shared memory by bulk copies
+    int32_t n_stages = 0;           // stages of the staged form (2 or 3: copies issued that many items ahead, less one)
     int32_t sorted = 0;             // rows of each tile packed in order of decreasing length
     int32_t resident = 0;           // resident schedule (a CTA keeps a tile's slice for all powers)
     int32_t wave_warps = kComputeWarps;   // compute warps of the MPK wavefront kernel
@@ -132,16 +134,24 @@ struct ExecArgs {
     const int32_t *row_map;      // chunk position -> row (rows sorted by length in a tile); null = identity
     const int4 *chunk_rec;       // per chunk {first row, rows, first entry / 32, width}
     int32_t stage_recs;          // chunk records one resident stage holds
+    int32_t n_stages;            // stages of the staged work-list form
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).
+// Plans with FP32 vectors keep the coefficient sum and the spectral scaling
+// in double-float (a value is the unevaluated sum hi + lo of two FP32
+// numbers); FP64 plans keep them in FP64.
 struct ChebArgs {
     ExecArgs e;
-    void *ring;             // 3 vector blocks (n x 2) cycling v_{k-2}, v_{k-1}, v_k
-    double *acc;            // n x 2 FP64 coefficient sum
-    const double *coef;     // device copy of all coefficients (interleaved complex)
+    void *ring;             // 3 vector blocks (n x G) cycling v_{k-2}, v_{k-1}, v_k
+    void *acc;              // n x G coefficient sum: FP64 (FP64 plans) or
+                            // double-float pairs (hi, lo) per column (FP32 plans)
+    const double *coef;     // FP64 coefficients, G per k (interleaved complex for G = 2)
+    const float4 *coef_df;  // double-float coefficients per k: (re hi, re lo, im hi, im lo)
     double alpha, beta;     // Ahat v = alpha*(A v) + beta*v with alpha = 1/r, beta = -c/r
+    float alpha_hi, alpha_lo, beta_hi, beta_lo, c_hi, c_lo;   // the same as double-float pairs
     int32_t k0;             // powers already computed before this sweep
+    int32_t pw;             // powers of this sweep
 };
 
 // Launch-wide arguments of a batched wavefront (several plans, one launch).

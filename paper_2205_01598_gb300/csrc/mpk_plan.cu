@@ -943,11 +943,21 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             pl->staged = 0;
             pl->smem_bytes = 2 * res_need;
         } else {
-            const size_t need = 2 * (size_t)pl->stage_entries * (size_t)(4 + pl->val_bytes);
-            pl->staged = (o->tune & MPK_TUNE_STAGE) && need + 1024 <= (size_t)prop.sharedMemPerBlockOptin;
-            pl->smem_bytes = pl->staged ? need : 0;
+            // staged work-list form (block widths 1 and 2): three stages, so
+            // that each copy is issued two items ahead, when the wanted CTAs
+            // per SM (ctas_per_sm, default 2) still fit; else two
+            const size_t optin = (size_t)prop.sharedMemPerBlockOptin, per_sm = (size_t)prop.sharedMemPerMultiprocessor;
+            const size_t want = (size_t)(o->ctas_per_sm > 0 ? o->ctas_per_sm : 2);
+            int nst = 0;
+            if ((o->tune & MPK_TUNE_STAGE) && o->nrhs <= 2) {
+                if (3 * res_need + 1024 <= optin && want * (3 * res_need + 1024) <= per_sm) nst = 3;
+                else if (2 * res_need + 1024 <= optin) nst = 2;
+            }
+            pl->staged = nst > 0;
+            pl->n_stages = nst;
+            pl->smem_bytes = (size_t)nst * res_need;
         }
-        pl->wave_warps = pl->staged || pl->resident ? kComputeWarps : (pl->prec == MPK_F64 ? kFp64Warps : kFp32Warps);
+        pl->wave_warps = pl->resident ? kComputeWarps : (pl->prec == MPK_F64 ? kFp64Warps : kFp32Warps);
     }
 
     // 11. grid size, then the work list: a skewed diagonal order of the Lp
