@@ -53,8 +53,28 @@ typedef enum {
  *  MPK_F32_BF16VAL vectors and sums in FP32; diagonal entries kept in FP32,
  *                  off-diagonal values stored as BF16 when every one of them
  *                  is exactly representable in BF16 (else FP32; see
- *                  mpk_plan_stats.val_bytes).                                */
-typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2 } mpk_prec;
+ *                  mpk_plan_stats.val_bytes).
+ *  MPK_F64_DF      FP64 vectors x and Y (same layouts and element type as
+ *                  MPK_F64) with the arithmetic on the FP32 pipe in
+ *                  double-float: every value is held as an unevaluated sum
+ *                  hi + lo of two FP32 numbers (about 47 significant bits),
+ *                  each row sum is a compensated dot product (exact products
+ *                  by FMA, TwoSum of the partial sums, errors summed apart),
+ *                  and each output element is rounded once to FP64.  Matrix
+ *                  values are stored as FP32 when every one of them is
+ *                  exactly an FP32 number (val_bytes 4), else as (hi, lo)
+ *                  pairs (val_bytes 8).  The results of integer-valued
+ *                  inputs are exact while they stay below 2^47 in magnitude.
+ *                  Limits: block width nrhs = 1; every nonzero |a_ij| in
+ *                  [2^-60, 2^60] (else mpk_plan returns MPK_ERR_UNSUPPORTED);
+ *                  at run time max|x| * ||A||_inf^p must stay below 2^100
+ *                  (else the call reports MPK_ERR_UNSUPPORTED and Y is not
+ *                  valid); elements below 2^-100 in magnitude lose relative
+ *                  precision (their absolute error stays below 2^-140).
+ *                  mpk_run, mpk_run_host and mpk_baseline_run serve it (the
+ *                  baseline with the same arithmetic, bit for bit); the
+ *                  Chebyshev calls and batches return MPK_ERR_UNSUPPORTED.   */
+typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_F32_BF16VAL = 2, MPK_F64_DF = 3 } mpk_prec;
 
 /* Tuning bits of mpk_opts.tune (for autotuners; 0 = defaults).
  *  MPK_TUNE_STAGE       stage each work item's matrix slice in shared memory

@@ -31,10 +31,10 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_CUDA, MPK_ERR_OOM, MPK_ERR_TIMEOUT, MPK_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-MPK_F64, MPK_F32, MPK_F32_BF16VAL = 0, 1, 2
+MPK_F64, MPK_F32, MPK_F32_BF16VAL, MPK_F64_DF = 0, 1, 2, 3
 MPK_IO_PERMUTED, MPK_ASYNC, MPK_SWEEP_ONE = 1, 2, 4
 MPK_TUNE_STAGE, MPK_TUNE_EVICT_LAST, MPK_TUNE_NO_SORT, MPK_TUNE_RESIDENT = 1, 2, 4, 8
-PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL}
+PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL, "f64df": MPK_F64_DF}
 
 
 def _nvcc():
@@ -233,7 +233,7 @@ class Plan:
     @property
     def vec_dtype(self):
         import torch
-        return torch.float64 if self.prec == MPK_F64 else torch.float32
+        return torch.float64 if self.prec in (MPK_F64, MPK_F64_DF) else torch.float32
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

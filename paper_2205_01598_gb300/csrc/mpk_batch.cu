@@ -94,7 +94,8 @@ int build_batch(Batch *b, const mpk_plan_t *plans, int32_t count) {
     b->count = count;
     for (int32_t m = 0; m < count; m++) {
         Plan *pl = &plans[m]->pl;
-        if (pl->has_diag || pl->prec != plans[0]->pl.prec || pl->device != plans[0]->pl.device)
+        if (pl->has_diag || pl->prec == MPK_F64_DF || pl->prec != plans[0]->pl.prec ||
+            pl->device != plans[0]->pl.device)
             return MPK_ERR_UNSUPPORTED;
         b->plans.push_back(pl);
     }

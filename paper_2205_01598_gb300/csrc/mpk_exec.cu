@@ -33,6 +33,8 @@ template <typename MT>
 __device__ __forceinline__ double as_double(MT v) { return (double)v; }
 template <>
 __device__ __forceinline__ double as_double<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <>
+__device__ __forceinline__ double as_double<float2>(float2 v) { return (double)v.x + (double)v.y; }
 
 // ---------------------------------------------------------------- TMA / mbarrier helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -1299,6 +1301,177 @@ __global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
     resident_loop<ChebNode<VT, MT, DIAG, G>, MT>(ca.e, epoch, ca);
 }
 
+// ---------------------------------------------------------------- double-float MPK (MPK_F64_DF)
+// FP64 input and outputs with the arithmetic on the FP32 pipe in
+// double-float pairs.  x is split once into pairs (shadow block 0); power k
+// gathers its inputs from shadow block (k-1) mod 2 and writes y_k to Y (FP64)
+// and to shadow block k mod 2.  Overwriting block k mod 2 (power k-2) is
+// safe: a tile's power k waits for power k-1 on every tile that reads the
+// tile's rows (the dependency ranges are closed under that symmetry), and
+// those were the last readers of its rows of power k-2.
+
+// FP64 -> double-float pair.  For |v| in [2^-74, 2^101) by integer
+// operations: hi = the leading 24 significant bits (truncated), lo = the
+// remaining 29 bits, rounded to FP32 by the integer-to-float conversion and
+// scaled by an exact power of two (hi + lo = v within 2^-47 |v|).  Other
+// values (zero included) through the conversion instructions.
+__device__ __forceinline__ float2 f64_to_df(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const uint32_t H = (uint32_t)(b >> 32), L = (uint32_t)b;
+    const uint32_t e = (H >> 20) & 0x7FFu;
+    if (e < 949u || e > 1123u) {
+        const float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    }
+    const uint32_t hb = (H & 0x80000000u) | (((H & 0x7FFFFFFFu) - (896u << 20)) << 3) | (L >> 29);
+    float lo = __uint2float_rn(L & 0x1FFFFFFFu) * __uint_as_float((e - 948u) << 23);   // * 2^(e - 1075)
+    if (H & 0x80000000u) lo = -lo;
+    return make_float2(__uint_as_float(hb), lo);
+}
+
+// FP32 -> FP64: zero and normal numbers by integer operations (the exponent
+// rebiased, the significand widened; exact), subnormal, infinite and NaN
+// inputs through the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if ((u & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (e == 0u || e == 255u) return (double)f;
+    return __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + (896u << 20))), (int)(u << 29));
+}
+
+// (s, c) += a * x, x = xh + xl: the product a * xh split exactly by FMA, the
+// small cross terms added to its error, its high part added to s by TwoSum,
+// and every error summed in c (one step of the compensated dot product Dot2
+// of Ogita, Rump and Oishi).  Values are FP32 (exact) or pairs (hi, lo).
+__device__ __forceinline__ void df_term(float &s, float &c, float a, float2 x) {
+    float p, e, t, q;
+    two_prod(a, x.x, p, e);
+    e = fmaf(a, x.y, e);
+    two_sum(s, p, t, q);
+    s = t;
+    c += q + e;
+}
+__device__ __forceinline__ void df_term(float &s, float &c, float2 a, float2 x) {
+    float p, e, t, q;
+    two_prod(a.x, x.x, p, e);
+    e = fmaf(a.x, x.y, fmaf(a.y, x.x, e));
+    two_sum(s, p, t, q);
+    s = t;
+    c += q + e;
+}
+
+template <typename MT>
+struct DfNode {
+    static constexpr bool kL2First = true;   // power-1 slices prefetched into L2, as in the FP64 MPK
+    static constexpr bool kPipe = true;
+
+    __device__ __forceinline__ static const float2 *in_of(const ExecArgs &a, int32_t k) {
+        return a.shadow + (int64_t)((k - 1) & 1) * a.blk;
+    }
+    // row r of power k from its compensated sum (s, c): the normalised pair
+    // to the shadow, hi + lo rounded once to FP64 into Y
+    __device__ __forceinline__ static void row_out(const ExecArgs &a, int32_t k, int32_t r, float s, float c) {
+        float h, l;
+        two_sum(s, c, h, l);
+        a.shadow[(int64_t)(k & 1) * a.blk + r] = make_float2(h, l);
+        double y = f32_to_f64(h);
+        if (l != 0.f) y += f32_to_f64(l);
+        ((double *)a.Y)[(int64_t)(k - 1) * a.blk + r] = y;
+    }
+    // entries j0.. of the lane's row (stored order, padding skipped)
+    __device__ __forceinline__ static void entries(const ExecArgs &a, int64_t e0, int32_t j0, int32_t w,
+                                                   const float2 *xin, float &s, float &c) {
+        constexpr int B = 8;
+        for (; j0 < w; j0 += B) {
+            int32_t cols[B];
+            MT vals[B];
+            float2 g[B];
+#pragma unroll
+            for (int u = 0; u < B; u++) {
+                const bool in = j0 + u < w;
+                cols[u] = in ? __ldg(a.pcol + e0 + (int64_t)(j0 + u) * kChunk) : -1;
+                vals[u] = in ? __ldg((const MT *)a.pval + e0 + (int64_t)(j0 + u) * kChunk) : MT{};
+            }
+#pragma unroll
+            for (int u = 0; u < B; u++) g[u] = cols[u] >= 0 ? xin[cols[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < B; u++)
+                if (cols[u] >= 0) df_term(s, c, vals[u], g[u]);
+        }
+    }
+    __device__ __forceinline__ static void chunk(const ExecArgs &a, int32_t c, int lane, int32_t k) {
+        const int32_t row0 = __ldg(a.chunk_row + c);
+        const int32_t nrows = __ldg(a.chunk_row + c + 1) - row0;
+        if (lane >= nrows) return;
+        const int64_t off = __ldg(a.chunk_off + c);
+        const int32_t w = (int32_t)((__ldg(a.chunk_off + c + 1) - off) / kChunk);
+        const int32_t r = a.row_map ? __ldg(a.row_map + row0 + lane) : row0 + lane;
+        float s = 0.f, cc = 0.f;
+        entries(a, off + lane, 0, w, in_of(a, k), s, cc);
+        row_out(a, k, r, s, cc);
+    }
+    template <typename Extra, int PC>
+    __device__ __forceinline__ static void pipe_run(const ExecArgs &a, const Slice<MT, PC> &sl, int32_t t, int32_t k,
+                                                    int warp, int nwarps, int lane, const Extra &) {
+        const float2 *xin = in_of(a, k);
+        float2 g[PC][kPE];
+#pragma unroll
+        for (int i = 0; i < PC; i++)
+#pragma unroll
+            for (int u = 0; u < kPE; u++) g[i][u] = sl.col[i][u] >= 0 ? xin[sl.col[i][u]] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PC; i++) {
+            if (sl.row[i] < 0) continue;
+            float s = 0.f, cc = 0.f;
+#pragma unroll
+            for (int u = 0; u < kPE; u++)
+                if (sl.col[i][u] >= 0) df_term(s, cc, sl.val[i][u], g[i][u]);
+            if (sl.rec[i].w > kPE) entries(a, (int64_t)sl.rec[i].z * kChunk + lane, kPE, sl.rec[i].w, xin, s, cc);
+            row_out(a, k, sl.row[i], s, cc);
+        }
+        for (int32_t c = sl.c0 + warp + PC * nwarps; c < sl.c1; c += nwarps) chunk(a, c, lane, k);
+    }
+    template <bool STAGED>
+    __device__ __forceinline__ static void run(const ExecArgs &a, const MatView<MT, STAGED> &, int32_t t, int32_t k,
+                                               int warp, int nwarps, int lane, const int &) {
+        const int32_t c1 = __ldg(a.tile_chunk + t + 1);
+        for (int32_t c = __ldg(a.tile_chunk + t) + warp; c < c1; c += nwarps) chunk(a, c, lane, k);
+    }
+    // the resident and staged forms do not run double-float plans
+    __device__ __forceinline__ static void res_run(const ExecArgs &, const int4 *, const int32_t *, const MT *, int64_t,
+                                                   int32_t, int32_t, int, int, int, const int &) {}
+};
+
+template <typename MT>
+__global__ void MPK_WAVE_BOUNDS((kFp64Warps + 1) * 32) k_wave_df(ExecArgs a) {
+    const OnePlan src{a, (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u};
+    wave_loop<DfNode<MT>, MT, false, OnePlan, int, 1>(a, src, 0);
+}
+
+// Baseline power k of a double-float plan: one SpMV with the same row arithmetic.
+template <typename MT>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv_df(ExecArgs a, int32_t k) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = gw; c < a.n_chunks; c += nw) DfNode<MT>::chunk(a, (int32_t)c, lane, k);
+}
+
+// x (FP64, level order) -> double-float pairs in shadow block 0.  An |x_i|
+// above the plan's range limit (or a NaN) sets MPK_ERR_UNSUPPORTED in the
+// plan's error word.
+__global__ void k_df_split(int32_t n, const double *__restrict__ x, float2 *__restrict__ out, uint64_t lim_bits,
+                           int32_t *ctl) {
+    bool bad = false;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[r];
+        bad |= ((unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull) > lim_bits;
+        out[r] = f64_to_df(v);
+    }
+    if (bad) atomicCAS(ctl + CTL_ERR, 0, (int)MPK_ERR_UNSUPPORTED);
+}
+
 // ---------------------------------------------------------------- batched MPK
 // Plans of a batch may differ in block width and number of powers; the node
 // dispatches on the plan's nrhs.
@@ -1517,6 +1690,8 @@ const void *pick_res_cheb_g(const Plan *pl) {
 }
 const void *pick_res_cheb(const Plan *pl) { return pl->nrhs == 1 ? pick_res_cheb_g<1>(pl) : pick_res_cheb_g<2>(pl); }
 const void *pick_wave(const Plan *pl) {
+    if (pl->prec == MPK_F64_DF)
+        return pl->val_bytes == 4 ? (const void *)k_wave_df<float> : (const void *)k_wave_df<float2>;
     if (pl->resident) return pl->nrhs == 1 ? pick_res_w<1>(pl) : pick_res_w<2>(pl);
     return pl->staged ? pick_wave_t<true>(pl) : pick_wave_t<false>(pl);
 }
@@ -1547,7 +1722,7 @@ const void *pick_spmv(const Plan *pl) {
 // plan has no Chebyshev kernel); also raises the kernels' limit of dynamic
 // shared memory to what the plan needs.
 int wave_occupancy(const Plan *pl, int *wave_ctas, int *cheb_ctas) {
-    const void *fns[2] = {pick_wave(pl), pl->nrhs <= 2 ? pick_cheb(pl) : nullptr};
+    const void *fns[2] = {pick_wave(pl), pl->nrhs <= 2 && pl->prec != MPK_F64_DF ? pick_cheb(pl) : nullptr};
     const int threads[2] = {wave_threads(pl), cheb_threads(pl)};
     int occ[2] = {1 << 30, 1 << 30};
     for (int i = 0; i < 2; i++) {
@@ -1592,6 +1767,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.stage_entries = pl->stage_entries;
     a.tune = pl->tune;
     a.n_stages = pl->n_stages;
+    a.shadow = pl->d_shadow;
     return a;
 }
 
@@ -1623,9 +1799,18 @@ static int epoch_guard(Plan *pl, cudaStream_t st) {
     return MPK_OK;
 }
 
+// Double-float plans: x split into pairs (shadow block 0), with the range guard.
+static int df_split(Plan *pl, const void *x, cudaStream_t st) {
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)pl->n + 255) / 256, (int64_t)pl->num_sms * 8));
+    k_df_split<<<g, 256, 0, st>>>(pl->n, (const double *)x, pl->d_shadow, pl->df_xlim_bits, pl->d_ctl);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
 int launch_wavefront(Plan *pl, const void *x, void *Y, cudaStream_t st) {
     int rc = epoch_guard(pl, st);
     if (rc) return rc;
+    if (pl->prec == MPK_F64_DF && (rc = df_split(pl, x, st))) return rc;
     ExecArgs a = exec_args(pl, x, Y);
     a.drop_tile = pl->drop_tile;
     a.drop_k = pl->drop_k;
@@ -1636,6 +1821,21 @@ int launch_wavefront(Plan *pl, const void *x, void *Y, cudaStream_t st) {
 
 int launch_baseline(Plan *pl, const void *x, void *Y, cudaStream_t st) {
     ExecArgs a = exec_args(pl, x, Y);
+    if (pl->prec == MPK_F64_DF) {
+        int rc = df_split(pl, x, st);
+        if (rc) return rc;
+        const void *fn = pl->val_bytes == 4 ? (const void *)k_spmv_df<float> : (const void *)k_spmv_df<float2>;
+        int occ = 0;
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSpmvThreads, 0));
+        const int wpb = kSpmvThreads / 32;
+        const int64_t grid = std::max<int64_t>(
+            1, std::min<int64_t>((int64_t)pl->num_sms * std::max(1, occ), ((int64_t)pl->n_chunks + wpb - 1) / wpb));
+        for (int32_t k = 1; k <= pl->p; k++) {
+            void *args[] = {(void *)&a, (void *)&k};
+            MPK_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kSpmvThreads), args, 0, st));
+        }
+        return MPK_OK;
+    }
     const void *fn = pick_spmv(pl);
     int occ = 0;
     MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSpmvThreads, 0));
@@ -1791,8 +1991,7 @@ int mpk_baseline_run(mpk_plan_t plan, const void *x, void *Y, uint32_t flags) {
     if (rc) return rc;
     MPK_CUDA(cudaGetLastError());
     if (flags & MPK_ASYNC) return MPK_OK;
-    MPK_CUDA(cudaStreamSynchronize(pl->stream));
-    return MPK_OK;
+    return read_device_error(pl, pl->stream);   // the double-float range guard reports here
 }
 
 int mpk_permute_vectors(mpk_plan_t plan, const void *src, void *dst, int32_t count, int32_t elem_bytes,
@@ -1814,7 +2013,8 @@ int mpk_gershgorin(mpk_plan_t plan, double *lo, double *hi) {
     double *d = nullptr;
     int rc = dev_alloc<double>(nullptr, &d, (size_t)2 * grid);
     if (rc) return rc;
-    if (pl->val_bytes == 8) k_gersh<double><<<grid, 256, 0, st>>>(a, d);
+    if (pl->prec == MPK_F64_DF && pl->val_bytes == 8) k_gersh<float2><<<grid, 256, 0, st>>>(a, d);
+    else if (pl->val_bytes == 8) k_gersh<double><<<grid, 256, 0, st>>>(a, d);
     else if (pl->val_bytes == 4) k_gersh<float><<<grid, 256, 0, st>>>(a, d);
     else k_gersh<__nv_bfloat16><<<grid, 256, 0, st>>>(a, d);
     std::vector<double> h((size_t)2 * grid);
@@ -1846,6 +2046,7 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
     if (!plan || !coef || !x || !y || M < 1 || !(r != 0.0)) return MPK_ERR_INVALID;
     Plan *pl = &plan->pl;
     if (pl->nrhs != G) return MPK_ERR_INVALID;
+    if (pl->prec == MPK_F64_DF) return MPK_ERR_UNSUPPORTED;
     cudaStream_t st = pl->stream;
     const int eb = elem_bytes_of(pl);
     const bool df = eb == 4;   // FP32 vectors: double-float scaling and coefficient sum

@@ -107,6 +107,8 @@ struct Plan {
     cudaEvent_t io_ev[4] = {};            // staging buffers unpermuted [0..1] / copied out [2..3]
     void *d_cheb = nullptr;            // Chebyshev vector ring (lazily)
     size_t cheb_bytes = 0;
+    float2 *d_shadow = nullptr;        // double-float copies of the current and previous power (MPK_F64_DF)
+    uint64_t df_xlim_bits = 0;         // largest |x| (FP64 bit pattern) the double-float range allows
 };
 
 // Parameters of the wavefront / baseline kernels.
@@ -135,6 +137,7 @@ struct ExecArgs {
     const int4 *chunk_rec;       // per chunk {first row, rows, first entry / 32, width}
     int32_t stage_recs;          // chunk records one resident stage holds
     int32_t n_stages;            // stages of the staged work-list form
+    float2 *shadow;              // MPK_F64_DF: 2 blocks of n double-float pairs, power k in block k mod 2
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).
@@ -205,7 +208,8 @@ int wave_occupancy(const Plan *pl, int *wave_ctas, int *cheb_ctas);
 const void *batch_kernel(int prec);
 int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st, int threads = kWaveThreads);
 
-inline int elem_bytes_of(const Plan *pl) { return pl->prec == MPK_F64 ? 8 : 4; }
+inline bool is_f64_vec(int prec) { return prec == MPK_F64 || prec == MPK_F64_DF; }
+inline int elem_bytes_of(const Plan *pl) { return is_f64_vec(pl->prec) ? 8 : 4; }
 inline int wave_threads(const Plan *pl) { return pl->resident ? kResThreads : (pl->wave_warps + 1) * 32; }
 inline int cheb_threads(const Plan *pl) { return pl->resident ? kResThreads : kWaveThreads; }
 

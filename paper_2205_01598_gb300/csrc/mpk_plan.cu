@@ -421,6 +421,27 @@ __global__ void k_bf16_exact(int32_t n, const int32_t *prow, const int32_t *pcol
     }
 }
 
+// Double-float plans: flags[0] = 1 if some value is not exactly an FP32
+// number, flags[1] = 1 if some nonzero |value| lies outside [2^-60, 2^60];
+// *rowsum_bits = the largest row sum of |a_ij| (the bit pattern of a
+// non-negative double orders like the double, so an integer maximum works).
+__global__ void k_df_values(int32_t n, const int32_t *prow, const double *pval, int32_t *flags,
+                            unsigned long long *rowsum_bits) {
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double sum = 0.0;
+    int32_t inexact = 0, out = 0;
+    for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
+        const double v = pval[e], av = fabs(v);
+        sum += av;
+        inexact |= (double)(float)v != v;
+        out |= v != 0.0 && !(av >= 0x1p-60 && av <= 0x1p60);
+    }
+    if (inexact) atomicOr(flags, 1);
+    if (out) atomicOr(flags + 1, 1);
+    atomicMax(rowsum_bits, (unsigned long long)__double_as_longlong(sum));
+}
+
 // ---------------------------------------------------------------- packing
 // Entries of row r that go into the SELL arrays (all of them, or all but the
 // diagonal when the diagonal is stored apart).
@@ -469,6 +490,11 @@ template <> __device__ __forceinline__ double cvt_val<double>(double v) { return
 template <> __device__ __forceinline__ float cvt_val<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt_val<__nv_bfloat16>(double v) {
     return __float2bfloat16_rn((float)v);
+}
+// double-float pair: hi = v rounded to FP32, lo = the rest rounded to FP32
+template <> __device__ __forceinline__ float2 cvt_val<float2>(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
 }
 
 // Column-major SELL-32: entry j of lane l of chunk c sits at off[c] + 32*j + l.
@@ -580,7 +606,7 @@ void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
                   pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
-                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec};
+                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec, pl->d_shadow};
     for (void *p : ps)
         if (p) cudaFree(p);
     for (cudaEvent_t e : pl->io_ev)
@@ -739,6 +765,29 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     int split_diag = 0;
     if (pl->prec == MPK_F64) {
         pl->val_bytes = 8;
+    } else if (pl->prec == MPK_F64_DF) {
+        // FP32 values when every value is exactly one, else (hi, lo) pairs;
+        // the run-time range guard: max|x| * ||A||_inf^p < 2^100
+        int32_t *d_fl;
+        unsigned long long *d_rs;
+        MPK_TRY(S.alloc(&d_fl, 2));
+        MPK_TRY(S.alloc(&d_rs, 1));
+        MPK_CUDA(cudaMemsetAsync(d_fl, 0, 2 * sizeof(int32_t), st));
+        MPK_CUDA(cudaMemsetAsync(d_rs, 0, sizeof(unsigned long long), st));
+        if (nnz > 0) k_df_values<<<blocks_for(n, 256), 256, 0, st>>>(n, prow, pval, d_fl, d_rs);
+        int32_t h_fl[2] = {0, 0};
+        unsigned long long h_rs = 0;
+        MPK_CUDA(cudaMemcpyAsync(h_fl, d_fl, sizeof(h_fl), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaMemcpyAsync(&h_rs, d_rs, sizeof(h_rs), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        if (h_fl[1]) return MPK_ERR_UNSUPPORTED;
+        pl->val_bytes = h_fl[0] ? 8 : 4;
+        double norm;
+        memcpy(&norm, &h_rs, sizeof(norm));
+        const double lim = 100.0 - (double)p * std::log2(std::max(norm, 1.0));
+        if (lim < -60.0) return MPK_ERR_UNSUPPORTED;   // no input could stay in range
+        const double xlim = std::ldexp(1.0, (int)std::floor(lim));
+        memcpy(&pl->df_xlim_bits, &xlim, sizeof(xlim));
     } else if (pl->prec == MPK_F32) {
         pl->val_bytes = 4;
     } else {
@@ -797,7 +846,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     //    Resident schedule: a tile must fit one of the two shared-memory
     //    stages of its CTA; rows are at most max_row_len entries wide, so
     //    tile_rows * max_row_len entries (plus a record per chunk) bound it.
-    const bool want_res = (o->tune & MPK_TUNE_RESIDENT) && (o->nrhs == 1 || o->nrhs == 2);
+    const bool want_res = (o->tune & MPK_TUNE_RESIDENT) && (o->nrhs == 1 || o->nrhs == 2) && o->prec != MPK_F64_DF;
     const int res_per_sm = std::max(1, std::min(2, o->ctas_per_sm > 0 ? o->ctas_per_sm : 1));
     size_t res_stage = 0;
     if (want_res) {
@@ -885,9 +934,16 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
                                                               pl->d_chunk_rec);
     MPK_TRY(dev_alloc(pl, &pl->d_pcol, (size_t)total));
     if (split_diag) MPK_TRY(dev_alloc(pl, &pl->d_diag, (size_t)n));
+    if (pl->prec == MPK_F64_DF) MPK_TRY(dev_alloc(pl, &pl->d_shadow, 2 * (size_t)n));
     {
         const unsigned nbk = blocks_for((int64_t)pl->n_chunks * kChunk, 256);
-        if (pl->val_bytes == 8) {
+        if (pl->prec == MPK_F64_DF && pl->val_bytes == 8) {
+            float2 *v;
+            MPK_TRY(dev_alloc(pl, &v, (size_t)total));
+            pl->d_pval = v;
+            k_pack<float2><<<nbk, 256, 0, st>>>(pl->n_chunks, pl->d_chunk_row, pl->d_chunk_off, pl->d_row_map, prow,
+                                                pcol, pval, split_diag, pl->d_pcol, v, pl->d_diag);
+        } else if (pl->val_bytes == 8) {
             double *v;
             MPK_TRY(dev_alloc(pl, &v, (size_t)total));
             pl->d_pval = v;
@@ -949,7 +1005,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             const size_t optin = (size_t)prop.sharedMemPerBlockOptin, per_sm = (size_t)prop.sharedMemPerMultiprocessor;
             const size_t want = (size_t)(o->ctas_per_sm > 0 ? o->ctas_per_sm : 2);
             int nst = 0;
-            if ((o->tune & MPK_TUNE_STAGE) && o->nrhs <= 2) {
+            if ((o->tune & MPK_TUNE_STAGE) && o->nrhs <= 2 && o->prec != MPK_F64_DF) {
                 if (3 * res_need + 1024 <= optin && want * (3 * res_need + 1024) <= per_sm) nst = 3;
                 else if (2 * res_need + 1024 <= optin) nst = 2;
             }
@@ -957,7 +1013,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             pl->n_stages = nst;
             pl->smem_bytes = (size_t)nst * res_need;
         }
-        pl->wave_warps = pl->resident ? kComputeWarps : (pl->prec == MPK_F64 ? kFp64Warps : kFp32Warps);
+        pl->wave_warps = pl->resident ? kComputeWarps : (is_f64_vec(pl->prec) ? kFp64Warps : kFp32Warps);
     }
 
     // 11. grid size, then the work list: a skewed diagonal order of the Lp
@@ -981,7 +1037,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         } else {
             pl->resident = 0;
             pl->smem_bytes = 0;
-            pl->wave_warps = pl->prec == MPK_F64 ? kFp64Warps : kFp32Warps;
+            pl->wave_warps = is_f64_vec(pl->prec) ? kFp64Warps : kFp32Warps;
         }
     }
     if (!pl->resident) {
@@ -1136,7 +1192,8 @@ int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out) {
     if (A->n < 1 || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return MPK_ERR_INVALID;
     if (p < 1 || p > kMaxP) return MPK_ERR_INVALID;
     if (o->nrhs < 1 || o->nrhs > kMaxNrhs) return MPK_ERR_INVALID;
-    if (o->prec < MPK_F64 || o->prec > MPK_F32_BF16VAL) return MPK_ERR_INVALID;
+    if (o->prec < MPK_F64 || o->prec > MPK_F64_DF) return MPK_ERR_INVALID;
+    if (o->prec == MPK_F64_DF && o->nrhs != 1) return MPK_ERR_UNSUPPORTED;
     if (!(o->safety_f > 0.0) || o->cache_bytes < 0.0 || o->tile_rows < 0 || o->ctas_per_sm < 0) return MPK_ERR_INVALID;
     mpk_plan_s *h = new (std::nothrow) mpk_plan_s();
     if (!h) return MPK_ERR_OOM;

@@ -88,7 +88,7 @@ int mpk_autotune(const mpk_csr *A, int32_t k, const mpk_opts *base, double min_t
                  int32_t n_cand, int32_t *best) {
     if (!A || !base || !cand || !best || n_cand < 1 || k < 1 || k > kMaxP) return MPK_ERR_INVALID;
     *best = -1;
-    const size_t eb = base->prec == MPK_F64 ? 8 : 4;
+    const size_t eb = is_f64_vec(base->prec) ? 8 : 4;
     const size_t vec = (size_t)A->n * (size_t)std::max(1, base->nrhs) * eb;
     int32_t qmax = 1;
     for (int32_t c = 0; c < n_cand; c++) qmax = std::max(qmax, std::min(std::max(1, cand[c].p_sweep), k));
