@@ -108,6 +108,9 @@ def _load():
             lib.oracle_permute_csr.argtypes = [i32, i32p, i32p, f64p, i32p, i32p, i32p, i32p, f64p]
             lib.oracle_level_groups.argtypes = [i32, f64p, i32, f64, f64, i32p]
             lib.oracle_level_groups.restype = i32
+            lib.oracle_recursive_levels.argtypes = [i32, i32p, i32p, i32, f64p, i32, f64, f64, i32, i32p, i32p,
+                                                    C.POINTER(i32), i32p, C.POINTER(i32), i32p]
+            lib.oracle_recursive_levels.restype = i32
             lib.oracle_lp_order.argtypes = [i32, i32, i32p, i32p]
             lib.oracle_lp_order.restype = C.c_int64
             lib.oracle_lb_mpk.argtypes = [i32, i32p, i32p, f64p, i32, i32p, i32, i32, f64p, f64p]
@@ -180,6 +183,22 @@ def level_groups(level_weight, pm, f, C_bytes):
     gp = np.empty(w.shape[0] + 1, dtype=np.int32)
     G = lib.oracle_level_groups(w.shape[0], w, int(pm), float(f), float(C_bytes), gp)
     return gp[:G + 1].copy()
+
+
+def recursive_levels(A, weights, pm, f, C_bytes, s_max, root=0):
+    """Sec. 4.4 recursion: returns (perm, level_ptr, group_ptr, group_stage,
+    stages) with the finest levels, the groups as ranges of them, the stage
+    that made each group, and the number of stages that refined something."""
+    lib = _load()
+    n = A.n
+    perm = np.empty(n, dtype=np.int32)
+    lp = np.empty(n + 1, dtype=np.int32)
+    gp = np.empty(n + 1, dtype=np.int32)
+    gs = np.empty(n + 1, dtype=np.int32)
+    nl, ng = C.c_int32(), C.c_int32()
+    st = lib.oracle_recursive_levels(n, _i32(A.rowptr), _i32(A.col), int(root), _f64(weights), int(pm), float(f),
+                                     float(C_bytes), int(s_max), perm, lp, C.byref(nl), gp, C.byref(ng), gs)
+    return perm, lp[:nl.value + 1].copy(), gp[:ng.value + 1].copy(), gs[:ng.value].copy(), int(st)
 
 
 def lp_order(nlevels, pm):

@@ -181,6 +181,162 @@ int32_t oracle_level_groups(int32_t nlevels, const double *level_weight, int32_t
     return G;
 }
 
+/* ------------------------------------------------------------------ recursion
+ * Sec. 4.4: levels and level groups refined recursively inside bulky groups.
+ *
+ * Stage 0 is Sec. 4.1-4.2: the Eq. 3 levels (oracle_bfs_levels, root
+ * `root`), the level-consecutive renumbering (oracle_level_perm) and the
+ * greedy groups of Eq. 5 (oracle_level_groups) over the level weights, a
+ * level's weight being the sum of w[v] over its vertices.  A group is bulky
+ * when it violates Eq. 5: it holds a single level and (pm+1)*weight >= f*C.
+ * Then, for stages s = 0 .. s_max-1, every maximal run of consecutive bulky
+ * groups is refined:
+ *   - the subgraph induced by the run's vertices (edges of the stored
+ *     pattern between two vertices of the run) gets its own BFS levels by
+ *     Eq. 3, rooted at the run's first vertex in the current numbering; when
+ *     the search runs out, the run's lowest-numbered (current numbering)
+ *     unvisited vertex starts the next level (the restart rule of the
+ *     stage-0 levels);
+ *   - the run's vertices are renumbered by (sub-level, current number), in
+ *     place of the run;
+ *   - the run's groups are replaced by the Eq. 5 groups of its sub-levels,
+ *     which belong to stage s+1; bulky ones among them are refined at the
+ *     next stage.
+ * Readings where the paper is silent: the root of a subgraph's search and
+ * the restart rule inside it; "consecutive" bulky groups form one subgraph.
+ *
+ * Outputs (caller-allocated, size n or n+1): perm[new] = old; the finest
+ * levels level_ptr[0..*nlevels] (first new vertex of each; level_ptr[*nlevels]
+ * = n); the groups group_ptr[0..*ngroups] as ranges of those levels; and
+ * group_stage[g], the recursion stage that made group g.  The pattern must
+ * be structurally symmetric.  Returns the number of stages that refined
+ * something (0 .. s_max).
+ */
+static int32_t groups_of_levels(int32_t l0, int32_t l1, const double *lw, int32_t pm, double f, double C,
+                                int32_t *gp_out)
+{   /* Eq. 5 over levels l0..l1-1; group starts (absolute level indices) */
+    return oracle_level_groups(l1 - l0, lw + l0, pm, f, C, gp_out);
+}
+
+int32_t oracle_recursive_levels(int32_t n, const int32_t *rowptr, const int32_t *col, int32_t root,
+                                const double *w, int32_t pm, double f, double C, int32_t s_max,
+                                int32_t *perm, int32_t *level_ptr, int32_t *nlevels,
+                                int32_t *group_ptr, int32_t *ngroups, int32_t *group_stage)
+{
+    int32_t *level = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *iperm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t L = oracle_bfs_levels(n, rowptr, col, root, 0, level);
+    /* current state: perm / iperm, flat levels lp[0..L], groups gp[0..G] with stages gs[] */
+    int32_t *lp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    oracle_level_perm(n, level, L, perm, iperm, lp);
+    double *lw = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+    int32_t *gp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *gs = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    for (int32_t l = 0; l < L; l++) {
+        lw[l] = 0.0;
+        for (int32_t r = lp[l]; r < lp[l + 1]; r++) lw[l] += w[perm[r]];
+    }
+    int32_t G = oracle_level_groups(L, lw, pm, f, C, gp);
+    for (int32_t g = 0; g < G; g++) gs[g] = 0;
+
+    /* scratch for the next state */
+    int32_t *lp2 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *gp2 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t *gs2 = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    double *lw2 = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+    int32_t *perm2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *sub = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);      /* sub-level per run position */
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    const double budget = f * C;
+    int32_t stages = 0;
+
+    for (int32_t s = 0; s < s_max; s++) {
+        int32_t L2 = 0, G2 = 0, refined = 0;
+        memcpy(perm2, perm, sizeof(int32_t) * (size_t)n);
+        int32_t g = 0;
+        while (g < G) {
+            const int bulky = gp[g + 1] - gp[g] == 1 && (double)(pm + 1) * lw[gp[g]] >= budget;
+            if (!bulky) {   /* copy the group and its levels unchanged */
+                gp2[G2] = L2;
+                gs2[G2++] = gs[g];
+                for (int32_t l = gp[g]; l < gp[g + 1]; l++) {
+                    lp2[L2] = lp[l];
+                    lw2[L2++] = lw[l];
+                }
+                g++;
+                continue;
+            }
+            int32_t g1 = g;   /* maximal run of bulky groups g .. g1-1 */
+            while (g1 < G && gp[g1 + 1] - gp[g1] == 1 && (double)(pm + 1) * lw[gp[g1]] >= budget) g1++;
+            const int32_t a = lp[gp[g]], b = lp[gp[g1]], m = b - a;
+            /* Eq. 3 on the induced subgraph of rows a..b-1 (current numbering) */
+            for (int32_t i = 0; i < m; i++) sub[i] = -1;
+            int32_t head = 0, tail = 0, maxlev = -1, next = 0, start = 0;
+            for (;;) {
+                sub[start] = maxlev + 1;
+                queue[tail++] = start;
+                while (head < tail) {
+                    const int32_t u = queue[head++];
+                    if (sub[u] > maxlev) maxlev = sub[u];
+                    const int32_t ou = perm[a + u];
+                    for (int32_t e = rowptr[ou]; e < rowptr[ou + 1]; e++) {
+                        const int32_t v = iperm[col[e]] - a;
+                        if (v >= 0 && v < m && sub[v] < 0) { sub[v] = sub[u] + 1; queue[tail++] = v; }
+                    }
+                }
+                while (next < m && sub[next] >= 0) next++;
+                if (next == m) break;
+                start = next;
+            }
+            const int32_t Ls = maxlev + 1;
+            /* renumber by (sub-level, current number): stable counting sort */
+            for (int32_t l = 0; l <= Ls; l++) tmp[l] = 0;
+            for (int32_t i = 0; i < m; i++) tmp[sub[i] + 1]++;
+            for (int32_t l = 0; l < Ls; l++) tmp[l + 1] += tmp[l];
+            const int32_t lbase = L2;
+            for (int32_t l = 0; l < Ls; l++) {
+                lp2[L2 + l] = a + tmp[l];
+                lw2[L2 + l] = 0.0;
+            }
+            for (int32_t i = 0; i < m; i++) {
+                const int32_t r = a + tmp[sub[i]]++;
+                perm2[r] = perm[a + i];
+                lw2[L2 + sub[i]] += w[perm[a + i]];
+            }
+            L2 += Ls;
+            /* Eq. 5 groups of the sub-levels, stage s+1 */
+            const int32_t Gs = groups_of_levels(lbase, L2, lw2, pm, f, C, tmp);
+            for (int32_t q = 0; q < Gs; q++) {
+                gp2[G2] = lbase + tmp[q];
+                gs2[G2++] = s + 1;
+            }
+            refined = 1;
+            g = g1;
+        }
+        lp2[L2] = n;
+        gp2[G2] = L2;
+        if (!refined) break;
+        stages = s + 1;
+        memcpy(perm, perm2, sizeof(int32_t) * (size_t)n);
+        for (int32_t r = 0; r < n; r++) iperm[perm[r]] = r;
+        memcpy(lp, lp2, sizeof(int32_t) * ((size_t)L2 + 1));
+        memcpy(lw, lw2, sizeof(double) * (size_t)L2);
+        memcpy(gp, gp2, sizeof(int32_t) * ((size_t)G2 + 1));
+        memcpy(gs, gs2, sizeof(int32_t) * (size_t)G2);
+        L = L2;
+        G = G2;
+    }
+    memcpy(level_ptr, lp, sizeof(int32_t) * ((size_t)L + 1));
+    memcpy(group_ptr, gp, sizeof(int32_t) * ((size_t)G + 1));
+    memcpy(group_stage, gs, sizeof(int32_t) * (size_t)G);
+    *nlevels = L;
+    *ngroups = G;
+    free(level); free(iperm); free(lp); free(lw); free(gp); free(gs); free(lp2); free(gp2); free(gs2);
+    free(lw2); free(perm2); free(sub); free(queue); free(tmp);
+    return stages;
+}
+
 /* ------------------------------------------------------------------ Lp order
  * Fig. 5 (Sec. 4.2): diagonals d = i + p ascending from 1 to L_m + pm - 1;
  * inside a diagonal, p ascending from max(1, d - L_m + 1) to min(d, pm);
