@@ -137,6 +137,15 @@ typedef struct {
                               power k trails power k-1 beyond what the
                               dependencies need; < 0 = automatic (default)     */
     uint32_t tune;         /* MPK_TUNE_* bits                                   */
+    int32_t recursion;     /* s_m of Sec. 4.4: maximum recursion stage (0 =
+                              none, the default).  Runs of consecutive level
+                              groups that violate Eq. 5 (one level each) are
+                              refined by the BFS levels of the subgraph they
+                              induce, rooted at the run's first row, and the
+                              Eq. 5 groups of those sub-levels, stage after
+                              stage; the issue order then places each item by
+                              its latest dependency (the "diamond" of Sec. 4.4)
+                              instead of one slope for all tiles.             */
 } mpk_opts;
 
 /* Summary of a plan (all host values).                                    */
@@ -161,6 +170,7 @@ typedef struct {
     int32_t sorted;        /* 1 if rows are sorted by length inside each tile    */
     int32_t resident;      /* 1 if the plan runs the resident schedule           */
     int32_t dep_span;      /* widest forward dependency span, in tiles          */
+    int32_t rec_stages;    /* recursion stages that refined something (Sec. 4.4) */
 } mpk_plan_stats;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -197,7 +207,9 @@ int mpk_plan_features(mpk_plan_t plan, float *out, int32_t count);
 
 /* Copies plan arrays to caller-allocated DEVICE buffers; any may be NULL.
  *  perm[n]        perm[new] = old (Sec. 4.5: recovers the original order)
- *  level_ptr[L+1] first new row of each level (Fig. 3e); level_ptr[L] = n
+ *  level_ptr[L+1] first new row of each level (Fig. 3e); level_ptr[L] = n;
+ *                 with recursion (Sec. 4.4) the finest levels: the levels
+ *                 of the runs that were refined replaced by their sub-levels
  *  group_ptr[G+1] first level of each level group; group_ptr[G] = L
  *  level[n]       Eq. 3 level of each ORIGINAL vertex                      */
 int mpk_plan_perm(mpk_plan_t plan, int32_t *perm, int32_t *level_ptr, int32_t *group_ptr,

@@ -78,11 +78,13 @@ struct Plan {
     int64_t stage_entries = 0;      // capacity of one stage in packed entries
     size_t smem_bytes = 0;          // dynamic shared memory per wavefront CTA
     // host copies kept to build the issue order of shorter sweeps
-    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_hi, h_work;
+    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_lo, h_dep_hi, h_work;
     int32_t *d_work_rem = nullptr;  // issue order for rem_p powers (Chebyshev remainder sweep)
     int32_t rem_p = 0;
 
-    std::vector<int32_t> h_level_ptr, h_group_ptr;
+    std::vector<int32_t> h_level_ptr, h_group_ptr;   // finest levels (after recursion) and their groups
+    std::vector<int32_t> h_group_stage;              // recursion stage that made each group (Sec. 4.4)
+    int32_t rec_stages = 0;                          // stages of recursion that refined something
 
     // device arrays (plan-owned)
     int32_t *d_perm = nullptr, *d_iperm = nullptr, *d_level = nullptr;

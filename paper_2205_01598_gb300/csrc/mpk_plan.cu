@@ -583,6 +583,58 @@ __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 // Temporary device buffers of the planner, freed on scope exit.
+// ---------------------------------------------------------------- recursion (Sec. 4.4)
+// The rows being refined are the runs of bulky level groups: run i covers
+// rows run_a[i] .. and the compacted indices run_base[i] .. run_base[i+1]-1.
+// comp_row[j] = the row of compacted index j; run_of[r] = run of row r (-1 if
+// none, preset), comp_of[r] = compacted index of row r.
+__global__ void k_runs_index(int32_t nruns, const int32_t *run_a, const int32_t *run_base, int32_t m,
+                             int32_t *comp_row, int32_t *run_of, int32_t *comp_of) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    int32_t lo = 0, hi = nruns - 1;   // the run with run_base[i] <= j < run_base[i+1]
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (run_base[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    const int32_t r = run_a[lo] + (j - run_base[lo]);
+    comp_row[j] = r;
+    run_of[r] = lo;
+    comp_of[r] = j;
+}
+
+// The subgraph each run induces: compacted vertex j keeps the columns of its
+// row that lie in the same run, as compacted indices (the stored order).
+__global__ void k_sub_len(int32_t m, const int32_t *comp_row, const int32_t *prow, const int32_t *pcol,
+                          const int32_t *run_of, int32_t *len) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int32_t r = comp_row[j], ri = run_of[r];
+    int32_t c = 0;
+    for (int32_t e = prow[r]; e < prow[r + 1]; e++) c += run_of[pcol[e]] == ri;
+    len[j] = c;
+}
+__global__ void k_sub_fill(int32_t m, const int32_t *comp_row, const int32_t *prow, const int32_t *pcol,
+                           const int32_t *run_of, const int32_t *comp_of, const int32_t *srow, int32_t *scol) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int32_t r = comp_row[j], ri = run_of[r];
+    int32_t o = srow[j];
+    for (int32_t e = prow[r]; e < prow[r + 1]; e++)
+        if (run_of[pcol[e]] == ri) scol[o++] = comp_of[pcol[e]];
+}
+
+// Renumbering of the runs by sub-level: ord[j] = the compacted vertex at
+// position j of the stable sort by sub-level (runs stay in their blocks,
+// their sub-levels being numbered run after run), so the row of compacted
+// index j receives the vertex of row comp_row[ord[j]].
+__global__ void k_apply_sub_order(int32_t m, const int32_t *ord, const int32_t *comp_row, const int32_t *perm_in,
+                                  int32_t *perm_out) {
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) perm_out[comp_row[j]] = perm_in[comp_row[ord[j]]];
+}
+
 struct Scratch {
     std::vector<void *> ptrs;
     ~Scratch() {
@@ -612,6 +664,193 @@ void free_plan(Plan *pl) {
     for (cudaEvent_t e : pl->io_ev)
         if (e) cudaEventDestroy(e);
     if (pl->copy_stream) cudaStreamDestroy(pl->copy_stream);
+}
+
+// Stable LSD radix sort (8-bit digits) of the n keys in kA (values in
+// [0, maxkey]); on return kA holds the sorted keys and vA the input position
+// of each (ties keep their input order).  kB, vB and hist (256 counters per
+// tile of kRsTile keys) are scratch.
+static int radix_sort_keys(int32_t n, int32_t maxkey, int32_t *&kA, int32_t *&kB, int32_t *&vA, int32_t *&vB,
+                           int32_t *hist, cudaStream_t st) {
+    const int32_t nb = (int32_t)((n + kRsTile - 1) / kRsTile);
+    int passes = 0;
+    for (uint32_t m = (uint32_t)maxkey; m; m >>= 8) passes++;
+    if (passes == 0) passes = 1;
+    bool first = true;
+    for (int ps = 0; ps < passes; ps++) {
+        k_rs_hist<<<nb, kRsThreads, 0, st>>>(kA, n, 8 * ps, hist, nb);
+        MPK_TRY(exclusive_scan<int32_t>(hist, hist, (int64_t)256 * nb, st, nullptr));
+        k_rs_scatter<<<nb, kRsThreads, 0, st>>>(kA, first ? nullptr : vA, kB, vB, n, 8 * ps, hist, nb);
+        first = false;
+        std::swap(kA, kB);
+        std::swap(vA, vB);
+    }
+    return MPK_OK;
+}
+
+// P A P^T with sorted rows for the permutation pl->d_perm (and its inverse).
+static int permute_matrix(Plan *pl, const mpk_csr *A, int32_t *prow, int32_t *plen, int32_t *pcol, double *pval,
+                          cudaStream_t st) {
+    const int32_t n = pl->n;
+    k_inverse_perm<<<blocks_for(n, 256), 256, 0, st>>>(n, pl->d_perm, pl->d_iperm);
+    MPK_CUDA(cudaMemsetAsync(plen + n, 0, sizeof(int32_t), st));
+    k_perm_len<<<blocks_for(n, 256), 256, 0, st>>>(n, A->rowptr, pl->d_perm, plen);
+    MPK_TRY(exclusive_scan<int32_t>(plen, prow, (int64_t)n + 1, st, nullptr));
+    k_perm_fill<<<blocks_for(n, 128), 128, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm, pl->d_iperm, prow,
+                                                    pcol, pval);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
+// Sec. 4.4: up to s_max stages, every maximal run of consecutive bulky level
+// groups (a single level with (p+1) * weight >= f * C) is refined by the
+// levels of the subgraph it induces: one cooperative BFS over the union of
+// the runs' subgraphs (its components come run after run in the current
+// numbering, so the restart rule roots each run at its first vertex, as a
+// separate search per run would), a stable sort of the runs' rows by
+// sub-level, and Eq. 5 groups of the sub-levels.  Updates the permutation,
+// P A P^T (prow, plen, pcol, pval), the finest levels pl->h_level_ptr with
+// their stored entries lnnz, the groups pl->h_group_ptr and their stages.
+static int refine_levels(Plan *pl, const mpk_csr *A, int32_t p, int32_t s_max, double bpe, double budget,
+                         int32_t *prow, int32_t *plen, int32_t *pcol, double *pval, std::vector<int64_t> &lnnz,
+                         int32_t *kA, int32_t *kB, int32_t *vA, int32_t *vB, int32_t *hist, Scratch &S,
+                         cudaStream_t st, uint64_t timeout_ns) {
+    const int32_t n = pl->n;
+    std::vector<int32_t> &lp = pl->h_level_ptr, &gp = pl->h_group_ptr;
+    pl->h_group_stage.assign(gp.size() - 1, 0);
+    int32_t *run_of, *comp_of, *comp_row, *slen, *srow, *scol, *slev, *queue, *perm2, *d_meta, *d_lp;
+    BfsCtl *bc;
+    MPK_TRY(S.alloc(&run_of, (size_t)n));
+    MPK_TRY(S.alloc(&comp_of, (size_t)n));
+    MPK_TRY(S.alloc(&comp_row, (size_t)n));
+    MPK_TRY(S.alloc(&slen, (size_t)n + 1));
+    MPK_TRY(S.alloc(&srow, (size_t)n + 1));
+    MPK_TRY(S.alloc(&scol, (size_t)std::max<int64_t>(1, A->nnz)));
+    MPK_TRY(S.alloc(&slev, (size_t)n));
+    MPK_TRY(S.alloc(&queue, (size_t)n));
+    MPK_TRY(S.alloc(&perm2, (size_t)n));
+    MPK_TRY(S.alloc(&d_meta, 2 * (size_t)n + 2));
+    MPK_TRY(S.alloc(&d_lp, (size_t)n + 1));
+    MPK_TRY(S.alloc(&bc, 1));
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, 512, 0));
+    if (occ < 1) return MPK_ERR_CUDA;
+    const int bfs_grid = pl->num_sms * std::min(occ, 2);
+    for (int32_t s = 0; s < s_max; s++) {
+        const int32_t G = (int32_t)gp.size() - 1;
+        auto bulky = [&](int32_t g) {
+            return gp[g + 1] - gp[g] == 1 && (double)(p + 1) * (double)lnnz[gp[g]] * bpe >= budget;
+        };
+        std::vector<int32_t> rg0, rg1, run_a, run_base(1, 0);
+        for (int32_t g = 0; g < G;) {
+            if (!bulky(g)) { g++; continue; }
+            int32_t g1 = g;
+            while (g1 < G && bulky(g1)) g1++;
+            rg0.push_back(g);
+            rg1.push_back(g1);
+            run_a.push_back(lp[gp[g]]);
+            run_base.push_back(run_base.back() + (lp[gp[g1]] - lp[gp[g]]));
+            g = g1;
+        }
+        const int32_t nruns = (int32_t)rg0.size();
+        if (nruns == 0) break;
+        const int32_t m = run_base.back();
+        // the union of the runs' induced subgraphs, compacted
+        MPK_CUDA(cudaMemcpyAsync(d_meta, run_a.data(), sizeof(int32_t) * nruns, cudaMemcpyHostToDevice, st));
+        MPK_CUDA(cudaMemcpyAsync(d_meta + nruns, run_base.data(), sizeof(int32_t) * (nruns + 1), cudaMemcpyHostToDevice,
+                                 st));
+        MPK_CUDA(cudaMemsetAsync(run_of, 0xff, sizeof(int32_t) * (size_t)n, st));
+        k_runs_index<<<blocks_for(m, 256), 256, 0, st>>>(nruns, d_meta, d_meta + nruns, m, comp_row, run_of, comp_of);
+        k_sub_len<<<blocks_for(m, 256), 256, 0, st>>>(m, comp_row, prow, pcol, run_of, slen);
+        MPK_CUDA(cudaMemsetAsync(slen + m, 0, sizeof(int32_t), st));
+        MPK_TRY(exclusive_scan<int32_t>(slen, srow, (int64_t)m + 1, st, nullptr));
+        k_sub_fill<<<blocks_for(m, 256), 256, 0, st>>>(m, comp_row, prow, pcol, run_of, comp_of, srow, scol);
+        // Eq. 3 on it, rooted at compacted vertex 0 (the first run's first row)
+        MPK_CUDA(cudaMemsetAsync(slev, 0xff, sizeof(int32_t) * (size_t)m, st));
+        MPK_CUDA(cudaMemsetAsync(bc, 0, sizeof(BfsCtl), st));
+        {
+            const int32_t *no = nullptr;
+            int32_t root = 0, mm = m;
+            uint64_t tns = timeout_ns;
+            void *args[] = {(void *)&mm, (void *)&srow, (void *)&scol, (void *)&no, (void *)&no, (void *)&root,
+                            (void *)&slev, (void *)&queue, (void *)&bc, (void *)&tns};
+            MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(bfs_grid), dim3(512), args, 0, st));
+        }
+        BfsCtl h_bc;
+        MPK_CUDA(cudaMemcpyAsync(&h_bc, bc, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        if (h_bc.err) return h_bc.err;
+        const int32_t Ls = h_bc.nlevels;
+        if (Ls < 1 || Ls > m) return MPK_ERR_CUDA;
+        // stable sort of the compacted vertices by sub-level; new permutation
+        MPK_CUDA(cudaMemcpyAsync(kA, slev, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, st));
+        MPK_TRY(radix_sort_keys(m, Ls - 1, kA, kB, vA, vB, hist, st));
+        k_level_ptr<<<blocks_for(m, 256), 256, 0, st>>>(m, kA, d_lp, Ls);
+        MPK_CUDA(cudaMemcpyAsync(perm2, pl->d_perm, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        k_apply_sub_order<<<blocks_for(m, 256), 256, 0, st>>>(m, vA, comp_row, pl->d_perm, perm2);
+        MPK_CUDA(cudaMemcpyAsync(pl->d_perm, perm2, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        MPK_TRY(permute_matrix(pl, A, prow, plen, pcol, pval, st));
+        std::vector<int32_t> slp((size_t)Ls + 1);
+        MPK_CUDA(cudaMemcpyAsync(slp.data(), d_lp, sizeof(int32_t) * ((size_t)Ls + 1), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        // the new finest levels: the runs' levels replaced by their sub-levels
+        // (run i owns the sub-levels starting in [run_base[i], run_base[i+1]))
+        std::vector<int32_t> nlp, ngp, ngs, run_l0(nruns), run_l1(nruns);
+        int32_t q = 0, sl = 0;
+        for (int32_t g = 0; g < G;) {
+            if (q < nruns && g == rg0[q]) {
+                run_l0[q] = (int32_t)nlp.size();
+                for (; sl < Ls && slp[sl] < run_base[q + 1]; sl++) nlp.push_back(run_a[q] + (slp[sl] - run_base[q]));
+                run_l1[q] = (int32_t)nlp.size();
+                ngp.push_back(-1 - q);   // placeholder: the run's groups come after its weights are known
+                ngs.push_back(s + 1);
+                g = rg1[q++];
+                continue;
+            }
+            ngp.push_back((int32_t)nlp.size());
+            ngs.push_back(pl->h_group_stage[g]);
+            for (int32_t l = gp[g]; l < gp[g + 1]; l++) nlp.push_back(lp[l]);
+            g++;
+        }
+        const int32_t L2 = (int32_t)nlp.size();
+        nlp.push_back(n);
+        // stored entries of the new levels
+        int64_t *d_ln;
+        MPK_TRY(S.alloc(&d_ln, (size_t)L2));
+        MPK_CUDA(cudaMemcpyAsync(d_lp, nlp.data(), sizeof(int32_t) * ((size_t)L2 + 1), cudaMemcpyHostToDevice, st));
+        k_level_nnz<<<blocks_for(L2, 256), 256, 0, st>>>(L2, d_lp, prow, d_ln);
+        std::vector<int64_t> nln((size_t)L2);
+        MPK_CUDA(cudaMemcpyAsync(nln.data(), d_ln, sizeof(int64_t) * (size_t)L2, cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        // Eq. 5 groups of each run's sub-levels, in place of its placeholder
+        std::vector<int32_t> fgp, fgs;
+        for (size_t k = 0; k < ngp.size(); k++) {
+            if (ngp[k] >= 0) {
+                fgp.push_back(ngp[k]);
+                fgs.push_back(ngs[k]);
+                continue;
+            }
+            const int32_t r = -1 - ngp[k];
+            for (int32_t s0 = run_l0[r]; s0 < run_l1[r];) {
+                double acc = (double)nln[s0] * bpe;
+                int32_t e = s0 + 1;
+                while (e < run_l1[r] && (double)(p + 1) * (acc + (double)nln[e] * bpe) < budget) {
+                    acc += (double)nln[e] * bpe;
+                    e++;
+                }
+                fgp.push_back(s0);
+                fgs.push_back(s + 1);
+                s0 = e;
+            }
+        }
+        fgp.push_back(L2);
+        lp = std::move(nlp);
+        lnnz = std::move(nln);
+        gp = std::move(fgp);
+        pl->h_group_stage = std::move(fgs);
+        pl->rec_stages = s + 1;
+    }
+    return MPK_OK;
 }
 
 int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
@@ -697,18 +936,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_TRY(S.alloc(&vB, (size_t)n));
     MPK_TRY(S.alloc(&hist, (size_t)256 * nb));
     MPK_CUDA(cudaMemcpyAsync(kA, pl->d_level, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    int passes = 0;
-    for (uint32_t m = (uint32_t)(L - 1); m; m >>= 8) passes++;
-    if (passes == 0) passes = 1;
-    bool first = true;
-    for (int ps = 0; ps < passes; ps++) {
-        k_rs_hist<<<nb, kRsThreads, 0, st>>>(kA, n, 8 * ps, hist, nb);
-        MPK_TRY(exclusive_scan<int32_t>(hist, hist, (int64_t)256 * nb, st, nullptr));
-        k_rs_scatter<<<nb, kRsThreads, 0, st>>>(kA, first ? nullptr : vA, kB, vB, n, 8 * ps, hist, nb);
-        first = false;
-        std::swap(kA, kB);
-        std::swap(vA, vB);
-    }
+    MPK_TRY(radix_sort_keys(n, L - 1, kA, kB, vA, vB, hist, st));
     MPK_TRY(dev_alloc(pl, &pl->d_perm, (size_t)n));
     MPK_TRY(dev_alloc(pl, &pl->d_iperm, (size_t)n));
     MPK_TRY(dev_alloc(pl, &pl->d_level_ptr, (size_t)L + 1));
@@ -836,6 +1064,25 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         gp.push_back(L);
         pl->h_group_ptr = gp;
         pl->n_groups = (int32_t)gp.size() - 1;
+    }
+
+    // 7b. recursion (Sec. 4.4): bulky groups refined by the levels of the
+    //     subgraphs they induce; the finest levels replace the levels
+    pl->h_group_stage.assign((size_t)pl->n_groups, 0);
+    if (o->recursion > 0) {
+        const double budget = pl->safety_f * pl->cache_bytes;
+        const double bpe = (double)(pl->val_bytes + 4);
+        MPK_TRY(refine_levels(pl, A, p, o->recursion, bpe, budget, prow, plen, pcol, pval, lnnz, kA, kB, vA, vB, hist,
+                              S, st, timeout_ns));
+        if (pl->rec_stages > 0) {
+            pl->n_levels = (int32_t)pl->h_level_ptr.size() - 1;
+            pl->n_groups = (int32_t)pl->h_group_ptr.size() - 1;
+            cudaFree(pl->d_level_ptr);
+            pl->d_level_ptr = nullptr;
+            MPK_TRY(dev_alloc(pl, &pl->d_level_ptr, pl->h_level_ptr.size()));
+            MPK_CUDA(cudaMemcpyAsync(pl->d_level_ptr, pl->h_level_ptr.data(), sizeof(int32_t) * pl->h_level_ptr.size(),
+                                     cudaMemcpyHostToDevice, st));
+        }
     }
 
     // 8. tiles (work items) inside groups, chunks of 32 rows inside tiles
@@ -1018,6 +1265,9 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
 
     // 11. grid size, then the work list: a skewed diagonal order of the Lp
     //     diagram over level groups (see order_items)
+    pl->h_dep_lo.resize((size_t)pl->n_tiles);
+    MPK_CUDA(cudaMemcpyAsync(pl->h_dep_lo.data(), pl->d_dep_lo, sizeof(int32_t) * pl->h_dep_lo.size(),
+                             cudaMemcpyDeviceToHost, st));
     pl->h_dep_hi.resize((size_t)pl->n_tiles);
     MPK_CUDA(cudaMemcpyAsync(pl->h_dep_hi.data(), pl->d_dep_hi, sizeof(int32_t) * pl->h_dep_hi.size(),
                              cudaMemcpyDeviceToHost, st));
@@ -1142,8 +1392,58 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
     struct Item { double key; int32_t k, t; };
     std::vector<Item> items;
     items.reserve((size_t)T * p);
-    for (int32_t k = 1; k <= p; k++)
-        for (int32_t t = 0; t < T; t++) items.push_back({v[t] + sigma * (k - 1), k, t});
+    if (pl->rec_stages == 0) {
+        for (int32_t k = 1; k <= p; k++)
+            for (int32_t t = 0; t < T; t++) items.push_back({v[t] + sigma * (k - 1), k, t});
+    } else {
+        // After recursion a tile next to a refined subgraph may read rows
+        // spread over all its sub-levels: one slope for every tile would
+        // have to cover the widest such span.  Instead each item is placed
+        // by its own latest dependency,
+        //   key(t, 1) = v(t),
+        //   key(t, k) = max(key(t, k-1) + 1, max over the tiles t' in
+        //               [dep_lo[t], dep_hi[t]] of key(t', k-1) + lag),
+        // so items near the boundary of a refined region are delayed as far
+        // as their dependencies need and no further (the "diamond" of
+        // Sec. 4.4); every dependency still comes strictly earlier.  The
+        // range maxima come from a sparse table per power.
+        const std::vector<int32_t> &lo = pl->h_dep_lo;
+        const double dl = std::max(lag, 0.5);
+        std::vector<double> key(v), nk((size_t)T);
+        int32_t levels = 1;
+        while ((1 << levels) < T) levels++;
+        std::vector<std::vector<double>> tab((size_t)levels + 1, std::vector<double>((size_t)T));
+        std::vector<int32_t> lg((size_t)T + 1, 0);
+        for (int32_t i = 2; i <= T; i++) lg[i] = lg[i / 2] + 1;
+        for (int32_t t = 0; t < T; t++) items.push_back({key[t], 1, t});
+        double slope_sum = 0.0;
+        for (int32_t k = 2; k <= p; k++) {
+            tab[0] = key;
+            for (int32_t j = 1; j <= levels; j++)
+                for (int32_t t = 0; t + (1 << j) <= T; t++)
+                    tab[j][t] = std::max(tab[j - 1][t], tab[j - 1][t + (1 << (j - 1))]);
+            for (int32_t t = 0; t < T; t++) {
+                double m = key[t] + 1.0;
+                const int32_t a = lo[t], b = hi[t];
+                if (a <= b) {
+                    const int32_t j = lg[b - a + 1];
+                    m = std::max(m, std::max(tab[j][a], tab[j][b - (1 << j) + 1]) + dl);
+                }
+                nk[t] = m;
+            }
+            key.swap(nk);
+            for (int32_t t = 0; t < T; t++) items.push_back({key[t], k, t});
+        }
+        for (int32_t t = 0; t < T; t++) slope_sum += p > 1 ? (key[t] - v[t]) / (p - 1) : 0.0;
+        work.resize(items.size());
+        std::sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
+            if (x.key != y.key) return x.key < y.key;
+            if (x.k != y.k) return x.k < y.k;
+            return x.t < y.t;
+        });
+        for (size_t i = 0; i < items.size(); i++) work[i] = (items[i].t << 8) | items[i].k;
+        return T > 0 ? slope_sum / T : 1.0;
+    }
     std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
         if (a.key != b.key) return a.key < b.key;
         if (a.k != b.k) return a.k < b.k;
@@ -1181,6 +1481,7 @@ int mpk_opts_default(mpk_opts *o) {
     o->stream = nullptr;
     o->lag = -1.0;
     o->tune = 0;
+    o->recursion = 0;
     return MPK_OK;
 }
 
@@ -1195,6 +1496,7 @@ int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out) {
     if (o->prec < MPK_F64 || o->prec > MPK_F64_DF) return MPK_ERR_INVALID;
     if (o->prec == MPK_F64_DF && o->nrhs != 1) return MPK_ERR_UNSUPPORTED;
     if (!(o->safety_f > 0.0) || o->cache_bytes < 0.0 || o->tile_rows < 0 || o->ctas_per_sm < 0) return MPK_ERR_INVALID;
+    if (o->recursion < 0 || o->recursion > 16) return MPK_ERR_INVALID;
     mpk_plan_s *h = new (std::nothrow) mpk_plan_s();
     if (!h) return MPK_ERR_OOM;
     int rc = build_plan(&h->pl, A, p, o);
@@ -1242,6 +1544,7 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->sorted = pl.sorted;
     s->resident = pl.resident;
     s->dep_span = pl.dep_span;
+    s->rec_stages = pl.rec_stages;
     s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
 }
