@@ -111,6 +111,10 @@ def _load():
             lib.oracle_recursive_levels.argtypes = [i32, i32p, i32p, i32, f64p, i32, f64, f64, i32, i32p, i32p,
                                                     C.POINTER(i32), i32p, C.POINTER(i32), i32p]
             lib.oracle_recursive_levels.restype = i32
+            lib.oracle_cg.argtypes = [i32, i32p, i32p, f64p, f64p, f64p, f64, i32, C.POINTER(f64)]
+            lib.oracle_cg.restype = i32
+            lib.oracle_sstep_cg.argtypes = [i32, i32p, i32p, f64p, f64p, f64p, i32, f64, f64, i32, C.POINTER(f64)]
+            lib.oracle_sstep_cg.restype = i32
             lib.oracle_lp_order.argtypes = [i32, i32, i32p, i32p]
             lib.oracle_lp_order.restype = C.c_int64
             lib.oracle_lb_mpk.argtypes = [i32, i32p, i32p, f64p, i32, i32p, i32, i32, f64p, f64p]
@@ -199,6 +203,27 @@ def recursive_levels(A, weights, pm, f, C_bytes, s_max, root=0):
     st = lib.oracle_recursive_levels(n, _i32(A.rowptr), _i32(A.col), int(root), _f64(weights), int(pm), float(f),
                                      float(C_bytes), int(s_max), perm, lp, C.byref(nl), gp, C.byref(ng), gs)
     return perm, lp[:nl.value + 1].copy(), gp[:ng.value + 1].copy(), gs[:ng.value].copy(), int(st)
+
+
+def cg(A, b, x0=None, tol=1e-10, max_iter=10000):
+    """Conjugate gradients (FP64): returns (x, steps, relres)."""
+    lib = _load()
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    rel = C.c_double()
+    it = lib.oracle_cg(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), _f64(b), x, float(tol), int(max_iter),
+                       C.byref(rel))
+    return x, int(it), rel.value
+
+
+def sstep_cg(A, b, s, rho, x0=None, tol=1e-10, max_steps=10000):
+    """s-step CG with the monomial basis scaled by rho^-k (FP64): returns
+    (x, steps, relres of the recurred residual)."""
+    lib = _load()
+    x = np.zeros(A.n) if x0 is None else _f64(x0).copy()
+    rel = C.c_double()
+    st = lib.oracle_sstep_cg(A.n, _i32(A.rowptr), _i32(A.col), _f64(A.val), _f64(b), x, int(s), float(rho),
+                             float(tol), int(max_steps), C.byref(rel))
+    return x, int(st), rel.value
 
 
 def lp_order(nlevels, pm):

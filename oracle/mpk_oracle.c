@@ -380,6 +380,123 @@ void oracle_lb_mpk(int32_t n, const int32_t *rowptr, const int32_t *col, const d
     }
 }
 
+/* ------------------------------------------------------------------ Krylov consumers of the MPK
+ * Sec. 1 and Sec. 8 name s-step Krylov methods as users of the MPK: their
+ * Krylov basis of s powers comes from one MPK.  Two FP64 references for a
+ * symmetric positive definite A, both stopping when ||r|| <= tol ||b||:
+ *
+ * Conjugate gradients (Hestenes and Stiefel, 1952): r = b - A x, p = r; per
+ * step q = A p, alpha = (r.r)/(p.q), x += alpha p, r -= alpha q,
+ * beta = (r.r)_new/(r.r)_old, p = r + beta p.  Returns the steps taken;
+ * *relres = ||r|| / ||b|| of the recurred residual.
+ */
+static double dotv(int32_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int32_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+int32_t oracle_cg(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b,
+                  double *x, double tol, int32_t max_iter, double *relres)
+{
+    double *r = (double *)malloc(sizeof(double) * (size_t)n), *p = (double *)malloc(sizeof(double) * (size_t)n);
+    double *q = (double *)malloc(sizeof(double) * (size_t)n);
+    oracle_spmv_rows(rowptr, col, val, 1, x, q, 0, n - 1);
+    for (int32_t i = 0; i < n; i++) { r[i] = b[i] - q[i]; p[i] = r[i]; }
+    const double bn = sqrt(dotv(n, b, b));
+    double rr = dotv(n, r, r);
+    int32_t it = 0;
+    while (it < max_iter && !(sqrt(rr) <= tol * bn)) {
+        oracle_spmv_rows(rowptr, col, val, 1, p, q, 0, n - 1);
+        const double alpha = rr / dotv(n, p, q);
+        for (int32_t i = 0; i < n; i++) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        const double rr2 = dotv(n, r, r);
+        const double beta = rr2 / rr;
+        for (int32_t i = 0; i < n; i++) p[i] = r[i] + beta * p[i];
+        rr = rr2;
+        it++;
+    }
+    *relres = bn > 0.0 ? sqrt(rr) / bn : 0.0;
+    free(r); free(p); free(q);
+    return it;
+}
+
+/* s-step conjugate gradients with the monomial basis (the communication-
+ * avoiding CG of Hoemmen's and Carson's work, restated): an outer iteration
+ * builds V = [p, Ap/rho, .., A^s p/rho^s, r, Ar/rho, .., A^(s-1) r/rho^(s-1)]
+ * with one MPK of [p r], its Gram matrix G = V^T V, and runs s CG steps on
+ * coordinate vectors of length 2s+1: with B the matrix of A in the basis
+ * (B[j+1][j] = rho inside each block), p' = e_0, r' = e_(s+1), x' = 0:
+ *   w = B p', alpha = (r'^T G r') / (p'^T G w), x' += alpha p',
+ *   r'' = r' - alpha w, beta = (r''^T G r'') / (r'^T G r'), p' = r'' + beta p',
+ * then x += V x', r = V r', p = V p'.  ||r||^2 = r'^T G r' gives the stop
+ * test after every inner step.  Returns the CG steps taken.
+ */
+int32_t oracle_sstep_cg(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b,
+                        double *x, int32_t s, double rho, double tol, int32_t max_steps, double *relres)
+{
+    const int32_t m = 2 * s + 1;
+    double *r = (double *)malloc(sizeof(double) * (size_t)n), *p = (double *)malloc(sizeof(double) * (size_t)n);
+    double *V = (double *)malloc(sizeof(double) * (size_t)n * m);
+    double *Y = (double *)malloc(sizeof(double) * (size_t)n * s);
+    double *G = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double xc[64], rc[64], pc[64], w[64], r2[64], Gv[64];
+    oracle_spmv_rows(rowptr, col, val, 1, x, r, 0, n - 1);
+    for (int32_t i = 0; i < n; i++) { r[i] = b[i] - r[i]; p[i] = r[i]; }
+    const double bn = sqrt(dotv(n, b, b));
+    double rr = dotv(n, r, r);
+    int32_t steps = 0;
+    while (steps < max_steps && !(sqrt(rr) <= tol * bn)) {
+        /* the basis: powers of p (0..s) and of r (0..s-1), scaled by rho^-k */
+        oracle_mpk(n, rowptr, col, val, s, 1, p, Y);
+        for (int32_t i = 0; i < n; i++) V[(size_t)i * m] = p[i];
+        for (int32_t k = 1; k <= s; k++)
+            for (int32_t i = 0; i < n; i++) V[(size_t)i * m + k] = Y[(size_t)(k - 1) * n + i] / pow(rho, k);
+        oracle_mpk(n, rowptr, col, val, s, 1, r, Y);
+        for (int32_t i = 0; i < n; i++) V[(size_t)i * m + s + 1] = r[i];
+        for (int32_t k = 1; k < s; k++)
+            for (int32_t i = 0; i < n; i++) V[(size_t)i * m + s + 1 + k] = Y[(size_t)(k - 1) * n + i] / pow(rho, k);
+        for (int32_t a = 0; a < m; a++)
+            for (int32_t c = 0; c < m; c++) {
+                double t = 0.0;
+                for (int32_t i = 0; i < n; i++) t += V[(size_t)i * m + a] * V[(size_t)i * m + c];
+                G[a * m + c] = t;
+            }
+        for (int32_t j = 0; j < m; j++) { xc[j] = 0.0; pc[j] = 0.0; rc[j] = 0.0; }
+        pc[0] = 1.0;
+        rc[s + 1] = 1.0;
+        for (int32_t j = 0; j < s && steps < max_steps && !(sqrt(rr) <= tol * bn); j++) {
+            for (int32_t a = 0; a < m; a++) w[a] = 0.0;
+            for (int32_t a = 0; a < s; a++) w[a + 1] += rho * pc[a];                 /* the p block */
+            for (int32_t a = 0; a < s - 1; a++) w[s + 2 + a] += rho * pc[s + 1 + a];  /* the r block */
+            for (int32_t a = 0; a < m; a++) { Gv[a] = 0.0; for (int32_t c = 0; c < m; c++) Gv[a] += G[a * m + c] * w[c]; }
+            double pGw = 0.0, rGr = 0.0;
+            for (int32_t a = 0; a < m; a++) pGw += pc[a] * Gv[a];
+            for (int32_t a = 0; a < m; a++) { double t = 0.0; for (int32_t c = 0; c < m; c++) t += G[a * m + c] * rc[c]; rGr += rc[a] * t; }
+            const double alpha = rGr / pGw;
+            for (int32_t a = 0; a < m; a++) { xc[a] += alpha * pc[a]; r2[a] = rc[a] - alpha * w[a]; }
+            double rGr2 = 0.0;
+            for (int32_t a = 0; a < m; a++) { double t = 0.0; for (int32_t c = 0; c < m; c++) t += G[a * m + c] * r2[c]; rGr2 += r2[a] * t; }
+            const double beta = rGr2 / rGr;
+            for (int32_t a = 0; a < m; a++) { pc[a] = r2[a] + beta * pc[a]; rc[a] = r2[a]; }
+            rr = rGr2 > 0.0 ? rGr2 : 0.0;
+            steps++;
+        }
+        for (int32_t i = 0; i < n; i++) {
+            double dx = 0.0, nr = 0.0, np = 0.0;
+            for (int32_t a = 0; a < m; a++) {
+                const double v = V[(size_t)i * m + a];
+                dx += xc[a] * v; nr += rc[a] * v; np += pc[a] * v;
+            }
+            x[i] += dx; r[i] = nr; p[i] = np;
+        }
+    }
+    *relres = bn > 0.0 ? sqrt(dotv(n, r, r)) / bn : 0.0;
+    free(r); free(p); free(V); free(Y); free(G);
+    return steps;
+}
+
 /* ------------------------------------------------------------------ Chebyshev
  * Gershgorin interval of A: [min_i (a_ii - sum_{j!=i} |a_ij|),
  * max_i (a_ii + sum_{j!=i} |a_ij|)].  Reading of the spectral scaling the
