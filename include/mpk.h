@@ -410,6 +410,37 @@ int mpk_mlp_loss_grad(mpk_mlp_t net, const float *X, const float *T, const float
 int mpk_mlp_adam_step(mpk_mlp_t net, float lr, float beta1, float beta2, float eps);
 int mpk_mlp_destroy(mpk_mlp_t net);
 
+/* ---------------------------------------------------------------- Krylov consumers
+ * Solvers of A x = b for a symmetric positive definite A that use the
+ * plan's kernels (Sec. 1: s-step Krylov methods get their Krylov basis of s
+ * powers from one MPK).  FP64 plans.  b, x: n DEVICE doubles in the caller's
+ * numbering (MPK_IO_PERMUTED: the plan's level order); x holds the initial
+ * guess on entry and the solution on return.  The iteration stops when the
+ * recurred residual satisfies ||r|| <= tol * ||b|| or after max_steps CG
+ * steps; *steps and *relres (HOST) receive the steps taken and
+ * ||r|| / ||b||.  Work space is plan-owned (allocated on first use).
+ * Calls synchronise the plan's stream.  Errors: MPK_ERR_INVALID (NULL
+ * pointers, tol < 0, max_steps < 0, a plan of another precision or width),
+ * MPK_ERR_OOM, MPK_ERR_CUDA, MPK_ERR_TIMEOUT.                               */
+
+/* Conjugate gradients (Hestenes and Stiefel): one SpMV and two inner
+ * products per step, the scalars kept on the device (the residual norm is
+ * read back every 8 steps, so up to 7 steps may follow convergence).  Plan:
+ * nrhs = 1, MPK_F64.                                                        */
+int mpk_cg(mpk_plan_t plan, const double *b, double *x, double tol, int32_t max_steps, int32_t *steps,
+           double *relres, uint32_t flags);
+
+/* s-step CG with the monomial basis: per s steps, ONE level-blocked MPK of
+ * the block [p r] (the plan: nrhs = 2, MPK_F64, p = s in 1..16) gives
+ * V = [p, Ap/rho, .., A^s p/rho^s, r, Ar/rho, .., A^(s-1) r/rho^(s-1)], its
+ * Gram matrix V^T V is summed on the GPU (FP64), s CG steps run on the
+ * coefficient vectors of the 2s+1 columns (with ||r||^2 from the Gram
+ * matrix), and one fused pass forms x, p and r.  rho scales the basis
+ * (0 = the larger end of the Gershgorin interval); the monomial basis loses
+ * accuracy as s grows, so s of 4..8 with rho near ||A|| is the usual choice. */
+int mpk_sstep_cg(mpk_plan_t plan, const double *b, double *x, double tol, int32_t max_steps, double rho,
+                 int32_t *steps, double *relres, uint32_t flags);
+
 /* Reorders vectors between the caller's numbering and the plan's level
  * order (Sec. 4.5: the permutation vector recovers the original order).
  * src and dst: count blocks of n x nrhs elements of elem_bytes (4 or 8)

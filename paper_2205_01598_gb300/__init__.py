@@ -26,7 +26,7 @@ _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libmpk.so")
 HEADER = os.path.join(_ROOT, "include", "mpk.h")
 SOURCES = ["mpk_plan.cu", "mpk_exec.cu", "mpk_batch.cu", "mpk_tune.cu", "mpk_mlp.cu", "mpk_inspect.cu", "mpk_poly.cu",
-           "mpk_host.cu", "mpk_calib.cu"]
+           "mpk_host.cu", "mpk_calib.cu", "mpk_krylov.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + os.path.join(_ROOT, "include")]
 
@@ -138,6 +138,8 @@ def load(path: str | None = None):
             "mpk_levels_noalloc": ([i32, i64, vp, vp, i32, vp, C.POINTER(i32), vp, f64], C.c_int),
             "mpk_plan_features": ([vp, vp, i32], C.c_int),
             "mpk_probe_fma": ([i32, i32, i64, vp, vp, C.POINTER(f64)], C.c_int),
+            "mpk_cg": ([vp, vp, vp, f64, i32, C.POINTER(i32), C.POINTER(f64), u32], C.c_int),
+            "mpk_sstep_cg": ([vp, vp, vp, f64, i32, f64, C.POINTER(i32), C.POINTER(f64), u32], C.c_int),
             "mpk_mlp_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
             "mpk_mlp_num_params": ([vp], C.c_int32),
             "mpk_mlp_get_params": ([vp, vp, i32], C.c_int),
@@ -502,6 +504,28 @@ def mpk_probe_fma(prec, sink, blocks_per_sm=8, iters=1 << 14, stream=None):
     _check(load().mpk_probe_fma(PRECISIONS[prec], int(blocks_per_sm), int(iters), _ptr(sink), _stream(stream),
                                 C.byref(fl)), "mpk_probe_fma")
     return fl.value
+
+
+def mpk_cg(plan: Plan, b, x, tol=1e-10, max_steps=10000, permuted=False):
+    """Conjugate gradients with the plan's SpMV (mpk_cg); b, x: n float64
+    CUDA tensors, x the initial guess, overwritten.  Returns (steps, relres)."""
+    import torch
+    bp, xp = _ptrs((b, plan.n, torch.float64, "b"), (x, plan.n, torch.float64, "x"))
+    st, rel = C.c_int32(), C.c_double()
+    _check(load().mpk_cg(plan.handle, bp, xp, float(tol), int(max_steps), C.byref(st), C.byref(rel),
+                         MPK_IO_PERMUTED if permuted else 0), "mpk_cg")
+    return st.value, rel.value
+
+
+def mpk_sstep_cg(plan: Plan, b, x, tol=1e-10, max_steps=10000, rho=0.0, permuted=False):
+    """s-step CG with one MPK of [p r] per s = plan.p steps (mpk_sstep_cg);
+    the plan has nrhs = 2.  Returns (steps, relres)."""
+    import torch
+    bp, xp = _ptrs((b, plan.n, torch.float64, "b"), (x, plan.n, torch.float64, "x"))
+    st, rel = C.c_int32(), C.c_double()
+    _check(load().mpk_sstep_cg(plan.handle, bp, xp, float(tol), int(max_steps), float(rho), C.byref(st),
+                               C.byref(rel), MPK_IO_PERMUTED if permuted else 0), "mpk_sstep_cg")
+    return st.value, rel.value
 
 
 class Batch:

@@ -1853,6 +1853,22 @@ int launch_baseline(Plan *pl, const void *x, void *Y, cudaStream_t st) {
     return MPK_OK;
 }
 
+// One SpMV of the plan's packed matrix, y = A x (x, y: n x nrhs in level
+// order, the plan's element type): the row kernel of the baseline.
+int launch_spmv1(Plan *pl, const void *x, void *y, cudaStream_t st) {
+    if (pl->prec == MPK_F64_DF) return MPK_ERR_UNSUPPORTED;
+    ExecArgs a = exec_args(pl, x, y);
+    const void *fn = pick_spmv(pl);
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSpmvThreads, 0));
+    const int wpb = kSpmvThreads / 32;
+    const int64_t grid = std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)pl->num_sms * std::max(1, occ), ((int64_t)pl->n_chunks + wpb - 1) / wpb));
+    void *args[] = {(void *)&a, (void *)&x, (void *)&y};
+    MPK_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kSpmvThreads), args, 0, st));
+    return MPK_OK;
+}
+
 int read_device_error(Plan *pl, cudaStream_t st) {
     int32_t w[CTL_WORDS];
     MPK_CUDA(cudaMemcpyAsync(w, pl->d_ctl, sizeof(w), cudaMemcpyDeviceToHost, st));

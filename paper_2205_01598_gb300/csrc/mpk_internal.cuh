@@ -110,6 +110,8 @@ struct Plan {
     void *d_cheb = nullptr;            // Chebyshev vector ring (lazily)
     size_t cheb_bytes = 0;
     float2 *d_shadow = nullptr;        // double-float copies of the current and previous power (MPK_F64_DF)
+    void *d_kry = nullptr;             // Krylov solver work space (lazily)
+    size_t kry_bytes = 0;
     uint64_t df_xlim_bits = 0;         // largest |x| (FP64 bit pattern) the double-float range allows
 };
 
@@ -198,6 +200,7 @@ int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t 
 // Execution entry points used across translation units.
 int launch_wavefront(Plan *pl, const void *x, void *Y, cudaStream_t st);
 int launch_baseline(Plan *pl, const void *x, void *Y, cudaStream_t st);
+int launch_spmv1(Plan *pl, const void *x, void *y, cudaStream_t st);
 int launch_cheb_sweep(Plan *pl, const ChebArgs &a, int32_t powers, cudaStream_t st);
 int read_device_error(Plan *pl, cudaStream_t st);
 int permute_vectors(Plan *pl, const void *src, void *dst, int32_t count, int32_t elem_bytes,

@@ -658,7 +658,7 @@ void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
                   pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
-                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec, pl->d_shadow};
+                  pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec, pl->d_shadow, pl->d_kry};
     for (void *p : ps)
         if (p) cudaFree(p);
     for (cudaEvent_t e : pl->io_ev)
