@@ -305,6 +305,20 @@ int mpk_cheb_coeffs_inverse(int32_t M, double c, double r, double *coef);
 int mpk_cheb_real(mpk_plan_t plan, const double *coef, int32_t M, double c, double r,
                   const void *x, double *y, uint32_t flags);
 
+/* Several time steps of the Chebyshev propagation (Sec. 7) in one call:
+ * y = U^nsteps x with U = sum_{k=0}^{M} coef_k T_k((A - c)/r), complex
+ * (plan nrhs = 2; coef: M+1 complex numbers, interleaved) or real (plan
+ * nrhs = 1; coef: M+1 reals), layouts and flags as mpk_cheb /
+ * mpk_cheb_real.  The nsteps*M matrix applications run as wavefront sweeps
+ * of the plan's p powers that continue across the time steps: the node of a
+ * step's last power hands its row of the step's result, in the storage
+ * precision, to the next step as v_0, so a plan with p >= nsteps*M runs the
+ * whole propagation in one launch.  Results equal nsteps calls of
+ * mpk_cheb / mpk_cheb_real whose x is the previous y in the storage
+ * precision.  MPK_ERR_INVALID if nsteps < 1 or as mpk_cheb.                */
+int mpk_cheb_steps(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, int32_t nsteps,
+                   const void *x, double *y, uint32_t flags);
+
 /* mpk_cheb and mpk_cheb_real with x and y in HOST memory (same layouts,
  * coefficients and flags): x is copied to a stream-ordered device buffer,
  * the propagation runs, and y is copied back, all on the plan's stream

@@ -127,6 +127,7 @@ def load(path: str | None = None):
             "mpk_cheb": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_host": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_real": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
+            "mpk_cheb_steps": ([vp, vp, i32, f64, f64, i32, vp, vp, u32], C.c_int),
             "mpk_cheb_real_host": ([vp, vp, i32, f64, f64, vp, vp, u32], C.c_int),
             "mpk_cheb_coeffs_heat": ([i32, f64, f64, f64, vp], C.c_int),
             "mpk_cheb_coeffs_inverse": ([i32, f64, f64, vp], C.c_int),
@@ -427,6 +428,27 @@ def mpk_cheb(plan: Plan, coef, c, r, x, y, permuted=False, asynchronous=False, o
     _check(load().mpk_cheb(plan.handle, ci.ctypes.data_as(C.c_void_p), coef.shape[0] - 1, float(c), float(r),
                            xp, yp,
                            _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)), "mpk_cheb")
+
+
+def mpk_cheb_steps(plan: Plan, coef, c, r, nsteps, x, y, permuted=False, asynchronous=False,
+                   one_power_per_launch=False):
+    """nsteps time steps of the Chebyshev propagation in sweeps that run
+    across the steps (mpk_cheb_steps): complex coef (plan nrhs = 2, x and y
+    of shape (n, 2)) or real coef (nrhs = 1, shape (n,)); y float64."""
+    import torch
+    coef = np.asarray(coef)
+    if plan.nrhs == 2:
+        cz = np.asarray(coef, dtype=np.complex128)
+        ci = np.empty(2 * cz.shape[0], dtype=np.float64)
+        ci[0::2], ci[1::2] = cz.real, cz.imag
+        M = cz.shape[0] - 1
+    else:
+        ci = np.ascontiguousarray(coef, dtype=np.float64)
+        M = ci.shape[0] - 1
+    xp, yp = _ptrs((x, plan.n * plan.nrhs, plan.vec_dtype, "x"), (y, plan.n * plan.nrhs, torch.float64, "y"))
+    _check(load().mpk_cheb_steps(plan.handle, ci.ctypes.data_as(C.c_void_p), M, float(c), float(r), int(nsteps), xp,
+                                 yp, _flags(permuted, asynchronous) | (MPK_SWEEP_ONE if one_power_per_launch else 0)),
+           "mpk_cheb_steps")
 
 
 def _host_vec(t, numel, dtype, name):

@@ -1085,22 +1085,39 @@ __device__ __forceinline__ void dot2_add(float &hi, float &lo, float ch, float c
 }
 
 // ---------------------------------------------------------------- Chebyshev
-// Node of a sweep: global power k = k0 + j, j = 1..pw.  With Ahat = (A - c)/r:
-//   v_1 = Ahat v_0,  v_k = 2 Ahat v_{k-1} - v_{k-2},  acc += coef_k v_k,
-// vectors in a ring of three blocks, G columns: G = 2 complex (re, im; the
-// Schroedinger propagator, complex coefficients), G = 1 real (the heat
-// propagator, real coefficients).  A v is summed in the storage precision.
-// FP64 plans do the rest in FP64.  FP32 plans do the spectral scaling in
-// double-float (the diagonal shift d - c exactly, then 1/r), round once to
-// FP32 at the recurrence, and keep the coefficient sum in double-float.
+// Node of a sweep.  The propagation runs T time steps of M powers each; the
+// node of global power g (k0 < g <= k0 + pw) is power k = g - step*M of time
+// step `step`.  With Ahat = (A - c)/r:
+//   v_1 = Ahat v_0,  v_k = 2 Ahat v_{k-1} - v_{k-2},  acc = sum_k coef_k v_k,
+// and v_0 of the next time step is the finished acc.  G columns: G = 2
+// complex (re, im; the Schroedinger propagator, complex coefficients), G = 1
+// real (the heat propagator, real coefficients).  A v is summed in the
+// storage precision.  FP64 plans do the rest in FP64.  FP32 plans do the
+// spectral scaling in double-float (the diagonal shift d - c exactly, then
+// 1/r), round once to FP32 at the recurrence, and keep acc in double-float.
 //
-// The coefficient sum is read and written every third power of a sweep and
-// at its last power: the node of power k holds v_{k-2}, v_{k-1} (its own
-// row of the two input vectors) and v_k, so it adds the terms not yet added
-// (local powers 3q+1 .. j) in ascending k.  The terms and their order are
-// the same however M is split into sweeps, so every split gives the same
-// bits.
-template <typename VT, typename MT, bool DIAG, int G>
+// Vectors live in a ring of three blocks.  Time step s holds v_0 .. v_M at
+// the virtual positions s*(M+1) + k, block = position mod 3.  The node of
+// power M writes the next step's v_0 (its row of the finished acc, in the
+// storage precision) at position s*(M+1) + M + 1, the block of v_{M-2},
+// whose last readers -- the neighbours' power M-1 and this node -- are done;
+// the next step's v_1 lands on v_{M-1}'s block, whose readers are the
+// power-M nodes it waits for.  So sweeps may run across time steps, and one
+// launch may hold several steps.
+//
+// acc (one array, only ever read by its own row) starts as coef_0 v_0 (a
+// kernel before the first sweep; for the later time steps the node of the
+// previous step's last power, right after it hands v_0 on).  It is read and
+// written every third power of a sweep, at the sweep's last power and at
+// power M: the node of power k holds v_{k-2} and v_{k-1} (its own row of the
+// two input vectors) and v_k, so it adds the terms not yet added, in
+// ascending k.  The terms and their order do not
+// depend on how the powers are split into sweeps, so every split gives the
+// same bits.
+// MULTI: the step-aware node (several time steps, v_0 handed on at a step's
+// last power); single-step propagations use the lean node (MULTI = false),
+// whose power k is simply k0 + j.
+template <typename VT, typename MT, bool DIAG, int G, bool MULTI>
 struct ChebNode {
     static constexpr bool kL2First = false;
     static_assert(G == 1 || G == 2, "real or complex vectors");
@@ -1110,15 +1127,36 @@ struct ChebNode {
     struct Vecs {
         const VT *yin, *yprev;
         VT *yout;
-        int32_t k;       // global power
+        VT *ynext;       // the next time step's v_0 (at the step's last power), else null
+        int32_t k;       // power within the time step, 1..M
         int32_t nterm;   // coefficient terms this node adds (0: none, else 1..3 ending at k)
     };
     __device__ __forceinline__ static Vecs vecs(const ExecArgs &a, const ChebArgs &ca, int32_t j) {
-        const int32_t k = ca.k0 + j;
         VT *ring = (VT *)ca.ring;
-        const int32_t flush = (j % 3 == 0 || j == ca.pw) ? j - 3 * ((j - 1) / 3) : 0;
-        return Vecs{ring + (int64_t)((k - 1) % 3) * a.blk, ring + (int64_t)((k + 1) % 3) * a.blk,   // (k-2) mod 3
-                    ring + (int64_t)(k % 3) * a.blk, k, flush};
+        if constexpr (!MULTI) {   // one time step: power k0 + j, flushes every third power of the sweep
+            const int32_t k = ca.k0 + j;
+            const int32_t flush = (j % 3 == 0 || j == ca.pw) ? j - 3 * ((j - 1) / 3) : 0;
+            return Vecs{ring + (int64_t)((k - 1) % 3) * a.blk, ring + (int64_t)((k + 1) % 3) * a.blk,
+                        ring + (int64_t)(k % 3) * a.blk, nullptr, k, flush};
+        }
+        // power k of time step `step` (32-bit arithmetic, no division by M:
+        // the host gives the sweep's first step and power)
+        int32_t step = ca.step0, k = ca.kin0 + j - 1;
+        while (k > ca.M) {
+            k -= ca.M;
+            step++;
+        }
+        const int32_t pos = step * (ca.M + 1) + k;   // virtual position of v_k
+        // flush points: every third power of the sweep, its last power and
+        // the last power of a time step; the terms not yet added start after
+        // the latest of the sweep's start, the last flush at a multiple of 3
+        // inside the sweep and the start of this time step
+        const int32_t last = max(ca.k0 + 3 * ((j - 1) / 3), step * ca.M);
+        const int32_t lo = last + 1 - step * ca.M;
+        const bool flush = j % 3 == 0 || k == ca.M || j == ca.pw;
+        auto blk = [&](int32_t q) { return ring + (int64_t)(q % 3) * a.blk; };
+        return Vecs{blk(pos - 1), blk(pos + 1),   // (pos - 2) mod 3
+                    blk(pos), (k == ca.M && ca.k0 + j < ca.total) ? blk(pos + 1) : nullptr, k, flush ? k - lo + 1 : 0};
     }
 
     // Row r of the node, given s = the row's sum of value * v_{k-1} over its
@@ -1160,6 +1198,16 @@ struct ChebNode {
                 if (v.nterm >= 3) add(pv, v.k - 2);
                 if (v.nterm >= 2) add(u, v.k - 1);
                 add(nv, v.k);
+                if (MULTI && v.ynext) {   // hand v_0 to the next step and restart acc as coef_0 v_0
+                    VT v0[G];
+#pragma unroll
+                    for (int q = 0; q < G; q++) {
+                        v0[q] = (VT)ac[q];
+                        v.ynext[G * (int64_t)r + q] = v0[q];
+                        ac[q] = 0.0;
+                    }
+                    add(v0, 0);
+                }
 #pragma unroll
                 for (int q = 0; q < G; q++) acc[q] = ac[q];
             }
@@ -1219,6 +1267,16 @@ struct ChebNode {
                 if (v.nterm >= 3) add(pv, v.k - 2);
                 if (v.nterm >= 2) add(u, v.k - 1);
                 add(nv, v.k);
+                if (MULTI && v.ynext) {   // hand v_0 (hi + lo rounded once to FP32) on, restart acc as coef_0 v_0
+                    VT v0[G];
+#pragma unroll
+                    for (int q = 0; q < G; q++) {
+                        v0[q] = ac[2 * q] + ac[2 * q + 1];
+                        v.ynext[G * (int64_t)r + q] = v0[q];
+                        ac[2 * q] = ac[2 * q + 1] = 0.f;
+                    }
+                    add(v0, 0);
+                }
                 if constexpr (G == 2)
                     *reinterpret_cast<float4 *>(acc) = make_float4(ac[0], ac[1], ac[2], ac[3]);
                 else
@@ -1289,16 +1347,17 @@ struct ChebNode {
     }
 };
 
-template <typename VT, typename MT, bool DIAG, bool STAGED, int G>
+template <typename VT, typename MT, bool DIAG, bool STAGED, int G, bool MULTI>
 __global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
     const OnePlan src{ca.e, (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u};
-    wave_loop<ChebNode<VT, MT, DIAG, G>, MT, STAGED>(ca.e, src, ca);
+    wave_loop<ChebNode<VT, MT, DIAG, G, MULTI>, MT, STAGED>(ca.e, src, ca);
 }
 
+// Two CTAs per SM must fit (the resident schedule's grid may use them).
 template <typename VT, typename MT, bool DIAG, int G>
-__global__ void __launch_bounds__(kResThreads) k_res_cheb(ChebArgs ca) {
+__global__ void __launch_bounds__(kResThreads, 2) k_res_cheb(ChebArgs ca) {
     const uint32_t epoch = (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u;
-    resident_loop<ChebNode<VT, MT, DIAG, G>, MT>(ca.e, epoch, ca);
+    resident_loop<ChebNode<VT, MT, DIAG, G, true>, MT>(ca.e, epoch, ca);
 }
 
 // ---------------------------------------------------------------- double-float MPK (MPK_F64_DF)
@@ -1517,9 +1576,9 @@ __global__ void __launch_bounds__(kWaveThreads, MPK_BATCH_MIN_BLOCKS) k_batch_wa
     wave_loop<BatchNode<VT, MT>, MT, false>(b.g, src, 0);
 }
 
-// acc = coef_0 * v_0 (complex for G = 2, real for G = 1), v_0 = ring block 0:
-// FP64 for FP64 plans, double-float pairs (the node's arithmetic, from zero)
-// for FP32 plans.
+// acc = coef_0 * v_0 (complex for G = 2, real for G = 1), v_0 = ring block 0,
+// before the first sweep: FP64 for FP64 plans, double-float pairs (the
+// node's arithmetic, from zero) for FP32 plans.
 template <int G>
 __global__ void k_cheb_init_f64(int32_t n, const double *v0, const double *coef, double *acc) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1664,15 +1723,21 @@ const void *pick_wave_t(const Plan *pl) {
     }
 }
 template <bool STAGED, int G>
-const void *pick_cheb_g(const Plan *pl) {
-    if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false, STAGED, G>;
-    if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED, G>;
-    if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED, G>;
-    return (const void *)k_cheb_wave<float, float, true, STAGED, G>;
+const void *pick_cheb_g(const Plan *pl, bool multi) {
+    if (multi) {
+        if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false, STAGED, G, true>;
+        if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED, G, true>;
+        if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED, G, true>;
+        return (const void *)k_cheb_wave<float, float, true, STAGED, G, true>;
+    }
+    if (pl->prec == MPK_F64) return (const void *)k_cheb_wave<double, double, false, STAGED, G, false>;
+    if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED, G, false>;
+    if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED, G, false>;
+    return (const void *)k_cheb_wave<float, float, true, STAGED, G, false>;
 }
 template <bool STAGED>
-const void *pick_cheb_t(const Plan *pl) {
-    return pl->nrhs == 1 ? pick_cheb_g<STAGED, 1>(pl) : pick_cheb_g<STAGED, 2>(pl);
+const void *pick_cheb_t(const Plan *pl, bool multi) {
+    return pl->nrhs == 1 ? pick_cheb_g<STAGED, 1>(pl, multi) : pick_cheb_g<STAGED, 2>(pl, multi);
 }
 template <int W>
 const void *pick_res_w(const Plan *pl) {
@@ -1704,9 +1769,9 @@ const void *batch_kernel(int prec) {
 
 namespace {
 
-const void *pick_cheb(const Plan *pl) {
+const void *pick_cheb(const Plan *pl, bool multi = true) {
     if (pl->resident) return pick_res_cheb(pl);
-    return pl->staged ? pick_cheb_t<true>(pl) : pick_cheb_t<false>(pl);
+    return pl->staged ? pick_cheb_t<true>(pl, multi) : pick_cheb_t<false>(pl, multi);
 }
 const void *pick_spmv(const Plan *pl) {
     if (pl->prec == MPK_F64) return spmv_ptr<double, double, false>(pl->nrhs);
@@ -1722,16 +1787,18 @@ const void *pick_spmv(const Plan *pl) {
 // plan has no Chebyshev kernel); also raises the kernels' limit of dynamic
 // shared memory to what the plan needs.
 int wave_occupancy(const Plan *pl, int *wave_ctas, int *cheb_ctas) {
-    const void *fns[2] = {pick_wave(pl), pl->nrhs <= 2 && pl->prec != MPK_F64_DF ? pick_cheb(pl) : nullptr};
-    const int threads[2] = {wave_threads(pl), cheb_threads(pl)};
-    int occ[2] = {1 << 30, 1 << 30};
-    for (int i = 0; i < 2; i++) {
+    // the MPK kernel, then the Chebyshev kernels (single- and multi-step)
+    const bool cheb = pl->nrhs <= 2 && pl->prec != MPK_F64_DF;
+    const void *fns[3] = {pick_wave(pl), cheb ? pick_cheb(pl, false) : nullptr, cheb ? pick_cheb(pl, true) : nullptr};
+    const int threads[3] = {wave_threads(pl), cheb_threads(pl), cheb_threads(pl)};
+    int occ[3] = {1 << 30, 1 << 30, 1 << 30};
+    for (int i = 0; i < 3; i++) {
         if (!fns[i]) continue;
         MPK_CUDA(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_bytes));
         MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[i], fns[i], threads[i], pl->smem_bytes));
     }
     *wave_ctas = occ[0];
-    *cheb_ctas = occ[1];
+    *cheb_ctas = std::min(occ[1], occ[2]);
     return MPK_OK;
 }
 
@@ -2058,8 +2125,9 @@ static inline void split_f64(double x, float &hi, float &lo) {
 // Chebyshev propagation with G vector columns (2: complex state and
 // coefficients, 1: real); the plan's block width must be G.
 static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
-                    uint32_t flags, int G) {
-    if (!plan || !coef || !x || !y || M < 1 || !(r != 0.0)) return MPK_ERR_INVALID;
+                    uint32_t flags, int G, int32_t T) {
+    if (!plan || !coef || !x || !y || M < 1 || T < 1 || !(r != 0.0) || (int64_t)M * T > INT32_MAX / 2)
+        return MPK_ERR_INVALID;
     Plan *pl = &plan->pl;
     if (pl->nrhs != G) return MPK_ERR_INVALID;
     if (pl->prec == MPK_F64_DF) return MPK_ERR_UNSUPPORTED;
@@ -2131,9 +2199,13 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
     ca.acc = acc;
     ca.coef = dcoef;
     ca.coef_df = dcoef_df;
+    ca.M = M;
+    ca.total = M * T;
+    // sweeps of p powers over all T*M powers: a sweep may run across time
+    // steps (the node of a step's last power hands v_0 to the next step)
     const int32_t sweep = (flags & MPK_SWEEP_ONE) ? 1 : pl->p;
-    for (int32_t k0 = 0; k0 < M; k0 += sweep) {
-        const int32_t pw = std::min(sweep, M - k0);
+    for (int32_t k0 = 0; k0 < ca.total; k0 += sweep) {
+        const int32_t pw = std::min(sweep, ca.total - k0);
         if ((rc = epoch_guard(pl, st))) return rc;
         ca.e = exec_args(pl, nullptr, nullptr);
         if (pw < pl->p) {   // a shorter last sweep has its own issue order
@@ -2156,8 +2228,11 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
         }
         ca.k0 = k0;
         ca.pw = pw;
+        ca.step0 = k0 / M;
+        ca.kin0 = k0 % M + 1;
         void *args[] = {(void *)&ca};
-        if ((rc = launch_coop(pick_cheb(pl), pl->cheb_grid, pl->smem_bytes, args, st, cheb_threads(pl)))) return rc;
+        if ((rc = launch_coop(pick_cheb(pl, T > 1), pl->cheb_grid, pl->smem_bytes, args, st, cheb_threads(pl))))
+            return rc;
     }
     if (df) {
         // double-float sum -> FP64 y (in place in level order, else gathered
@@ -2177,12 +2252,20 @@ static int cheb_run(mpk_plan_t plan, const double *coef, int32_t M, double c, do
 
 int mpk_cheb(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
              uint32_t flags) {
-    return cheb_run(plan, coef, M, c, r, x, y, flags, 2);
+    return cheb_run(plan, coef, M, c, r, x, y, flags, 2, 1);
 }
 
 int mpk_cheb_real(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, const void *x, double *y,
                   uint32_t flags) {
-    return cheb_run(plan, coef, M, c, r, x, y, flags, 1);
+    return cheb_run(plan, coef, M, c, r, x, y, flags, 1, 1);
+}
+
+int mpk_cheb_steps(mpk_plan_t plan, const double *coef, int32_t M, double c, double r, int32_t nsteps, const void *x,
+                   double *y, uint32_t flags) {
+    if (!plan) return MPK_ERR_INVALID;
+    const int32_t G = plan->pl.nrhs;
+    if (G != 1 && G != 2) return MPK_ERR_INVALID;
+    return cheb_run(plan, coef, M, c, r, x, y, flags, G, nsteps);
 }
 
 int mpk_plan_last_error(mpk_plan_t plan, int32_t *code, int32_t *power, int32_t *tile) {

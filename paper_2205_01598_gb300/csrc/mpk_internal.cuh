@@ -157,8 +157,11 @@ struct ChebArgs {
     const float4 *coef_df;  // double-float coefficients per k: (re hi, re lo, im hi, im lo)
     double alpha, beta;     // Ahat v = alpha*(A v) + beta*v with alpha = 1/r, beta = -c/r
     float alpha_hi, alpha_lo, beta_hi, beta_lo, c_hi, c_lo;   // the same as double-float pairs
-    int32_t k0;             // powers already computed before this sweep
+    int32_t k0;             // powers already computed before this sweep (all time steps)
     int32_t pw;             // powers of this sweep
+    int32_t M;              // powers (degree) of one time step
+    int32_t total;          // powers of the whole propagation (time steps x M)
+    int32_t step0, kin0;    // time step and power within it (1..M) of the sweep's first power
 };
 
 // Launch-wide arguments of a batched wavefront (several plans, one launch).
