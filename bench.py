@@ -568,7 +568,11 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     mpk.build()
     mpk.load()
-    plans, plans_unsorted, xs, Ys, flops, nnz_total, rows_total = [], [], [], [], 0.0, 0, 0
+    from paper_2205_01598_gb300 import planner as pln
+    net = pln.Planner.load() if os.path.exists(pln.WEIGHTS) else None
+    g8 = pln.grid()
+    plans, plans_unsorted, plans_tuned, xs, Ys, flops, nnz_total, rows_total = [], [], [], [], [], 0.0, 0, 0
+    options = []
     t0 = time.perf_counter()
     for m, seed, n, nrhs, p in specs:
         A = mats[m]
@@ -576,6 +580,21 @@ def run_batch(args):
         plan = mpk.mpk_plan(rp, cl, va, p, prec="f32", nrhs=nrhs)
         plans.append(plan)
         plans_unsorted.append(mpk.mpk_plan(rp, cl, va, p, prec="f32", nrhs=nrhs, tune=mpk.MPK_TUNE_NO_SORT))
+        # the member's own options: the learned planner's pick from the
+        # features of its default plan (the autotuner, searched for this p
+        # and width, without weights); the batch runs the work-list schedule,
+        # so a resident pick keeps its f and sweep with automatic work items
+        if net is not None:
+            i = int(net.choose(mpk.mpk_plan_features(plan))[0])
+            o = dict(pln.member_options(g8[i], p), source="mlp", grid_index=i)
+        else:
+            o = pln.plan_options(rp, cl, va, p, prec="f32", nrhs=nrhs, use_weights=False)
+        if o["tune"] & mpk.MPK_TUNE_RESIDENT:
+            o["tune"] &= ~mpk.MPK_TUNE_RESIDENT
+            o["tile_rows"], o["resident_pick"] = 0, True
+        options.append(o)
+        plans_tuned.append(mpk.mpk_plan(rp, cl, va, p, prec="f32", nrhs=nrhs, tile_rows=o["tile_rows"],
+                                        safety_f=o["safety_f"], tune=o["tune"], sweep=o["sweep"]))
         xs.append(torch.rand(A.n, nrhs, dtype=torch.float32, device="cuda"))
         Ys.append(torch.empty(p, A.n, nrhs, dtype=torch.float32, device="cuda"))
         flops += 2.0 * A.nnz * nrhs * p
@@ -583,9 +602,11 @@ def run_batch(args):
         rows_total += A.n
         del rp, cl, va
     t_plan = time.perf_counter() - t0
-    batch = mpk.mpk_batch_create(plans)
+    batch = mpk.mpk_batch_create(plans_tuned)
     binfo = mpk.mpk_batch_info(batch)
     mpk.mpk_batch_graph_capture(batch, xs, Ys)
+    batch_def = mpk.mpk_batch_create(plans)
+    mpk.mpk_batch_graph_capture(batch_def, xs, Ys)
     st = torch.cuda.current_stream()
 
     def timed(fn, steps, warmup, sampler=None):
@@ -606,19 +627,25 @@ def run_batch(args):
     ms = timed(lambda: mpk.mpk_batch_graph_launch(batch, asynchronous=True), args.steps, args.warmup, sampler)
     mpk.mpk_batch_graph_launch(batch)   # synchronous: surfaces device-side errors
 
-    def separate():
-        for plan, x, Y in zip(plans, xs, Ys):
-            mpk.mpk_run(plan, x, Y, permuted=True, asynchronous=True)
-
     def baseline(ps):
         for plan, x, Y in zip(ps, xs, Ys):
             mpk.mpk_baseline_run(plan, x, Y, permuted=True, asynchronous=True)
 
-    ms_sep = timed(separate, max(3, args.steps // 4), 2)
-    # the comparator gets the better of the two packings (rows sorted by length
-    # inside a work item cut padding but scatter single-vector writes)
-    ms_base = min(timed(lambda: baseline(plans), max(3, args.steps // 4), 2),
-                  timed(lambda: baseline(plans_unsorted), max(3, args.steps // 4), 2))
+    def separate(ps):
+        for plan, x, Y in zip(ps, xs, Ys):
+            mpk.mpk_run(plan, x, Y, permuted=True, asynchronous=True)
+
+    ms_def = timed(lambda: mpk.mpk_batch_graph_launch(batch_def, asynchronous=True), max(3, args.steps // 4), 2)
+    mpk.mpk_batch_graph_launch(batch_def)
+    ms_sep = timed(lambda: separate(plans_tuned), max(3, args.steps // 4), 2)
+    # the comparator gets the best of the packings (rows sorted by length
+    # inside a work item cut padding but scatter single-vector writes; the
+    # members' own work-item sizes)
+    ms_base = min(timed(lambda: baseline(ps), max(3, args.steps // 4), 2)
+                  for ps in (plans, plans_unsorted, plans_tuned))
+    kinds = {"one sweep": 0, "two sweeps": 0, "single-power sweeps": 0}
+    for o, (_, _, _, _, p) in zip(options, specs):
+        kinds["one sweep" if o["sweep"] == p else ("single-power sweeps" if o["sweep"] == 1 else "two sweeps")] += 1
     out = {
         "metric": "batched MPK GFLOP/s (sum 2*nnz*nrhs*p / t)", "value": round(flops / (ms * 1e-3) / 1e9, 3),
         "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -628,6 +655,12 @@ def run_batch(args):
                   "grid_ctas": binfo["grid_ctas"]},
         "speedup_vs_separate_launches": round(ms_sep / ms, 4),
         "speedup_vs_pxspmv": round(ms_base / ms, 4),
+        "member_options": {
+            "source": options[0]["source"] if options else None,
+            "sweep_kinds": kinds, "resident_picks_run_as_work_list": sum(1 for o in options if o.get("resident_pick")),
+            "per_member": [[o["tile_rows"], o["safety_f"], o["sweep"]] for o in options],
+            "per_member_fields": ["tile_rows (0 = automatic)", "safety_f", "sweep"]},
+        "default_options_batch": {"ms_per_step": round(ms_def, 4), "speedup_of_member_options": round(ms_def / ms, 4)},
         "separate_launches": {"ms_per_step": round(ms_sep, 4), "gpu_launches_per_step": count},
         "baseline_pxspmv": {"ms_per_step": round(ms_base, 4),
                             "gpu_launches_per_step": int(sum(s[4] for s in specs))},

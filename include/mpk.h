@@ -146,6 +146,17 @@ typedef struct {
                               stage; the issue order then places each item by
                               its latest dependency (the "diamond" of Sec. 4.4)
                               instead of one slope for all tiles.             */
+    int32_t sweep;         /* powers per sweep, q (p_m of Eq. 5); 0 = p, the
+                              default.  With q < p the issue order runs powers
+                              1..q over all tiles in the wavefront order, then
+                              q+1..2q, and so on, all in the one launch of
+                              mpk_run: the first power of a sweep waits on the
+                              flags of the last power of the one before, with
+                              no launch boundary.  The level groups of Eq. 5
+                              are sized for q powers (q = 1: power-major order,
+                              p SpMVs chained by point-to-point flags).  The
+                              resident schedule owns tiles for all p powers and
+                              is not used when q < p.                         */
 } mpk_opts;
 
 /* Summary of a plan (all host values).                                    */
@@ -171,6 +182,7 @@ typedef struct {
     int32_t resident;      /* 1 if the plan runs the resident schedule           */
     int32_t dep_span;      /* widest forward dependency span, in tiles          */
     int32_t rec_stages;    /* recursion stages that refined something (Sec. 4.4) */
+    int32_t sweep;         /* powers per sweep of the issue order (q <= p)       */
 } mpk_plan_stats;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -374,8 +386,10 @@ typedef struct {
     int32_t tile_rows;     /* in: rows per work item (0: automatic)           */
     double safety_f;       /* in: f of Eq. 5 (with the base C)                */
     uint32_t tune;         /* in: MPK_TUNE_* bits                             */
-    int32_t p_sweep;       /* in: powers per sweep (k = q*p_sweep + r: q
-                              sweeps of p_sweep powers and one of r)          */
+    int32_t p_sweep;       /* in: powers per sweep (mpk_opts.sweep: the k
+                              powers in one launch, sweeps of p_sweep; with
+                              MPK_TUNE_RESIDENT one plan and launch per sweep
+                              of p_sweep powers and one for the rest)         */
     double ms;             /* out: measured time of the k powers (ms), -1 if failed */
     int32_t status;        /* out: mpk_status of planning / running           */
 } mpk_tune_candidate;
@@ -389,7 +403,7 @@ typedef struct {
 int mpk_tune_default_grid(int32_t k, mpk_tune_candidate *out, int32_t max, int32_t *count);
 
 /* Times every candidate for the MPK of A with k powers (opts from *base with
- * the candidate's fields; each plan part run repeatedly until min_time_s),
+ * the candidate's fields; each plan run repeatedly until min_time_s),
  * writes ms / status into cand[], and *best = the index of the fastest.
  * Allocates temporary device vectors.  MPK_ERR_UNSUPPORTED if no candidate
  * ran; MPK_ERR_CUDA ends the search.                                        */

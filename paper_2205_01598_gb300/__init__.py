@@ -78,7 +78,8 @@ class mpk_opts(C.Structure):
     _fields_ = [("root", C.c_int32), ("cache_bytes", C.c_double), ("safety_f", C.c_double),
                 ("prec", C.c_int32), ("nrhs", C.c_int32), ("tile_rows", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("timeout_s", C.c_double), ("stream", C.c_void_p),
-                ("lag", C.c_double), ("tune", C.c_uint32), ("recursion", C.c_int32)]
+                ("lag", C.c_double), ("tune", C.c_uint32), ("recursion", C.c_int32),
+                ("sweep", C.c_int32)]
 
 
 class mpk_tune_candidate(C.Structure):
@@ -94,7 +95,8 @@ class mpk_plan_stats(C.Structure):
                 ("matrix_bytes", C.c_int64), ("device_bytes", C.c_int64), ("plan_ms", C.c_double),
                 ("cache_bytes", C.c_double), ("slope", C.c_double), ("staged", C.c_int32),
                 ("smem_bytes", C.c_int32), ("sorted", C.c_int32), ("resident", C.c_int32),
-                ("dep_span", C.c_int32), ("rec_stages", C.c_int32)]
+                ("dep_span", C.c_int32), ("rec_stages", C.c_int32),
+                ("sweep", C.c_int32)]
 
 
 _lib = None
@@ -252,9 +254,10 @@ def mpk_opts_default():
 
 def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=0.0, safety_f=0.5,
              prec="f64", nrhs=1, tile_rows=0, ctas_per_sm=0, timeout_s=2.0, lag=-1.0, tune=0,
-             recursion=0, stream=None) -> Plan:
+             recursion=0, sweep=0, stream=None) -> Plan:
     """Level-blocked plan of the CRS matrix (rowptr, col: int32 CUDA tensors,
-    val: float64 CUDA tensor) for powers 1..p (mpk_plan)."""
+    val: float64 CUDA tensor) for powers 1..p (mpk_plan); sweep = q < p runs
+    the powers in sweeps of q inside the one launch."""
     A = _csr(rowptr, col, val, assume_symmetric)
     lib = load()
     o = mpk_opts_default()
@@ -265,6 +268,7 @@ def mpk_plan(rowptr, col, val, p, *, assume_symmetric=True, root=0, cache_bytes=
     o.lag = float(lag)
     o.tune = int(tune)
     o.recursion = int(recursion)
+    o.sweep = int(sweep)
     h = C.c_void_p()
     _check(lib.mpk_plan(C.byref(A), int(p), C.byref(o), C.byref(h)), "mpk_plan")
     return Plan(h, int(p), int(nrhs), o.prec, A.n, stream)

@@ -85,6 +85,7 @@ struct Plan {
     std::vector<int32_t> h_level_ptr, h_group_ptr;   // finest levels (after recursion) and their groups
     std::vector<int32_t> h_group_stage;              // recursion stage that made each group (Sec. 4.4)
     int32_t rec_stages = 0;                          // stages of recursion that refined something
+    int32_t sweep = 0;                               // powers per sweep of the issue order (q of mpk_opts.sweep)
 
     // device arrays (plan-owned)
     int32_t *d_perm = nullptr, *d_iperm = nullptr, *d_level = nullptr;

@@ -860,6 +860,8 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     pl->n = A->n;
     pl->nnz = A->nnz;
     pl->p = p;
+    const int32_t q = o->sweep > 0 ? std::min(o->sweep, p) : p;   // p_m of Eq. 5
+    pl->sweep = q;
     pl->nrhs = o->nrhs;
     pl->prec = o->prec;
     pl->safety_f = o->safety_f;
@@ -1045,7 +1047,8 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         }
     }
 
-    // 7. level groups (Eq. 5): add levels while (p+1) * weight(T) < f * C
+    // 7. level groups (Eq. 5): add levels while (q+1) * weight(T) < f * C,
+    //    q the powers of one sweep
     {
         const double budget = pl->safety_f * pl->cache_bytes;
         const double bpe = (double)(pl->val_bytes + 4);
@@ -1054,7 +1057,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         while (s0 < L) {
             double acc = (double)lnnz[s0] * bpe;
             int32_t e = s0 + 1;
-            while (e < L && (double)(p + 1) * (acc + (double)lnnz[e] * bpe) < budget) {
+            while (e < L && (double)(q + 1) * (acc + (double)lnnz[e] * bpe) < budget) {
                 acc += (double)lnnz[e] * bpe;
                 e++;
             }
@@ -1072,7 +1075,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     if (o->recursion > 0) {
         const double budget = pl->safety_f * pl->cache_bytes;
         const double bpe = (double)(pl->val_bytes + 4);
-        MPK_TRY(refine_levels(pl, A, p, o->recursion, bpe, budget, prow, plen, pcol, pval, lnnz, kA, kB, vA, vB, hist,
+        MPK_TRY(refine_levels(pl, A, q, o->recursion, bpe, budget, prow, plen, pcol, pval, lnnz, kA, kB, vA, vB, hist,
                               S, st, timeout_ns));
         if (pl->rec_stages > 0) {
             pl->n_levels = (int32_t)pl->h_level_ptr.size() - 1;
@@ -1093,7 +1096,8 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     //    Resident schedule: a tile must fit one of the two shared-memory
     //    stages of its CTA; rows are at most max_row_len entries wide, so
     //    tile_rows * max_row_len entries (plus a record per chunk) bound it.
-    const bool want_res = (o->tune & MPK_TUNE_RESIDENT) && (o->nrhs == 1 || o->nrhs == 2) && o->prec != MPK_F64_DF;
+    const bool want_res =
+        (o->tune & MPK_TUNE_RESIDENT) && (o->nrhs == 1 || o->nrhs == 2) && o->prec != MPK_F64_DF && q == p;
     const int res_per_sm = std::max(1, std::min(2, o->ctas_per_sm > 0 ? o->ctas_per_sm : 1));
     size_t res_stage = 0;
     if (want_res) {
@@ -1371,9 +1375,13 @@ int static_levels_scratch(int32_t **out) {
 // (the paper's slope, i.e. p+1 level groups between the first and last power
 // front, the working set Eq. 5 budgets for).  Ties go to the lower power, so
 // dependencies always come first and in-order hand-out cannot deadlock.
+// With sweeps of q < p powers (Sec. 5.1 splits a power into sweeps) the
+// powers of sweep s = (k-1) / q come after every item of sweep s-1, each
+// sweep traversed as above with k - 1 replaced by its power within the sweep.
 double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &work) {
     const std::vector<int32_t> &tile_row = pl->h_tile_row, &group_tile = pl->h_group_tile, &hi = pl->h_dep_hi;
     const int32_t T = pl->n_tiles, G = pl->n_groups;
+    const int32_t q = pl->sweep > 0 ? std::min(pl->sweep, p) : p;
     std::vector<double> v((size_t)T);
     for (int32_t g = 0; g < G; g++) {
         const double r0 = tile_row[group_tile[g]], r1 = tile_row[group_tile[g + 1]];
@@ -1386,15 +1394,16 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
         // the order is shared by the MPK and the Chebyshev launches: size the
         // lag for the smaller of their grids
         const int32_t grid = pl->cheb_grid > 0 ? std::min(pl->grid_ctas, pl->cheb_grid) : pl->grid_ctas;
-        lag = 1.5 * (double)grid / ((double)p * tiles_per_group);
+        lag = 1.5 * (double)grid / ((double)q * tiles_per_group);
     }
     const double sigma = std::max(1.0, need + lag);
-    struct Item { double key; int32_t k, t; };
+    struct Item { int32_t s; double key; int32_t k, t; };
     std::vector<Item> items;
     items.reserve((size_t)T * p);
+    double slope = sigma;
     if (pl->rec_stages == 0) {
         for (int32_t k = 1; k <= p; k++)
-            for (int32_t t = 0; t < T; t++) items.push_back({v[t] + sigma * (k - 1), k, t});
+            for (int32_t t = 0; t < T; t++) items.push_back({(k - 1) / q, v[t] + sigma * ((k - 1) % q), k, t});
     } else {
         // After recursion a tile next to a refined subgraph may read rows
         // spread over all its sub-levels: one slope for every tile would
@@ -1406,7 +1415,8 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
         // so items near the boundary of a refined region are delayed as far
         // as their dependencies need and no further (the "diamond" of
         // Sec. 4.4); every dependency still comes strictly earlier.  The
-        // range maxima come from a sparse table per power.
+        // range maxima come from a sparse table per power.  The first power
+        // of every sweep starts again from v(t).
         const std::vector<int32_t> &lo = pl->h_dep_lo;
         const double dl = std::max(lag, 0.5);
         std::vector<double> key(v), nk((size_t)T);
@@ -1415,43 +1425,42 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
         std::vector<std::vector<double>> tab((size_t)levels + 1, std::vector<double>((size_t)T));
         std::vector<int32_t> lg((size_t)T + 1, 0);
         for (int32_t i = 2; i <= T; i++) lg[i] = lg[i / 2] + 1;
-        for (int32_t t = 0; t < T; t++) items.push_back({key[t], 1, t});
+        for (int32_t t = 0; t < T; t++) items.push_back({0, key[t], 1, t});
         double slope_sum = 0.0;
         for (int32_t k = 2; k <= p; k++) {
-            tab[0] = key;
-            for (int32_t j = 1; j <= levels; j++)
-                for (int32_t t = 0; t + (1 << j) <= T; t++)
-                    tab[j][t] = std::max(tab[j - 1][t], tab[j - 1][t + (1 << (j - 1))]);
-            for (int32_t t = 0; t < T; t++) {
-                double m = key[t] + 1.0;
-                const int32_t a = lo[t], b = hi[t];
-                if (a <= b) {
-                    const int32_t j = lg[b - a + 1];
-                    m = std::max(m, std::max(tab[j][a], tab[j][b - (1 << j) + 1]) + dl);
+            if ((k - 1) % q == 0) {
+                key = v;
+            } else {
+                tab[0] = key;
+                for (int32_t j = 1; j <= levels; j++)
+                    for (int32_t t = 0; t + (1 << j) <= T; t++)
+                        tab[j][t] = std::max(tab[j - 1][t], tab[j - 1][t + (1 << (j - 1))]);
+                for (int32_t t = 0; t < T; t++) {
+                    double m = key[t] + 1.0;
+                    const int32_t a = lo[t], b = hi[t];
+                    if (a <= b) {
+                        const int32_t j = lg[b - a + 1];
+                        m = std::max(m, std::max(tab[j][a], tab[j][b - (1 << j) + 1]) + dl);
+                    }
+                    nk[t] = m;
                 }
-                nk[t] = m;
+                key.swap(nk);
             }
-            key.swap(nk);
-            for (int32_t t = 0; t < T; t++) items.push_back({key[t], k, t});
+            if (k == q)
+                for (int32_t t = 0; t < T; t++) slope_sum += (key[t] - v[t]) / (q - 1);
+            for (int32_t t = 0; t < T; t++) items.push_back({(k - 1) / q, key[t], k, t});
         }
-        for (int32_t t = 0; t < T; t++) slope_sum += p > 1 ? (key[t] - v[t]) / (p - 1) : 0.0;
-        work.resize(items.size());
-        std::sort(items.begin(), items.end(), [](const Item &x, const Item &y) {
-            if (x.key != y.key) return x.key < y.key;
-            if (x.k != y.k) return x.k < y.k;
-            return x.t < y.t;
-        });
-        for (size_t i = 0; i < items.size(); i++) work[i] = (items[i].t << 8) | items[i].k;
-        return T > 0 ? slope_sum / T : 1.0;
+        slope = T > 0 && q > 1 ? slope_sum / T : 1.0;
     }
     std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+        if (a.s != b.s) return a.s < b.s;
         if (a.key != b.key) return a.key < b.key;
         if (a.k != b.k) return a.k < b.k;
         return a.t < b.t;
     });
     work.resize(items.size());
     for (size_t i = 0; i < items.size(); i++) work[i] = (items[i].t << 8) | items[i].k;
-    return sigma;
+    return slope;
 }
 
 int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st, int32_t *total) {
@@ -1482,6 +1491,7 @@ int mpk_opts_default(mpk_opts *o) {
     o->lag = -1.0;
     o->tune = 0;
     o->recursion = 0;
+    o->sweep = 0;
     return MPK_OK;
 }
 
@@ -1497,6 +1507,7 @@ int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out) {
     if (o->prec == MPK_F64_DF && o->nrhs != 1) return MPK_ERR_UNSUPPORTED;
     if (!(o->safety_f > 0.0) || o->cache_bytes < 0.0 || o->tile_rows < 0 || o->ctas_per_sm < 0) return MPK_ERR_INVALID;
     if (o->recursion < 0 || o->recursion > 16) return MPK_ERR_INVALID;
+    if (o->sweep < 0 || o->sweep > kMaxP) return MPK_ERR_INVALID;
     mpk_plan_s *h = new (std::nothrow) mpk_plan_s();
     if (!h) return MPK_ERR_OOM;
     int rc = build_plan(&h->pl, A, p, o);
@@ -1545,6 +1556,7 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->resident = pl.resident;
     s->dep_span = pl.dep_span;
     s->rec_stages = pl.rec_stages;
+    s->sweep = pl.sweep;
     s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
 }

@@ -1,5 +1,8 @@
 // Autotuner of the level-blocked MPK (the tuning of Sec. 6.1: p_m, C and the
-// split of a power k into sweeps, Sec. 5.1), measured on the GPU.
+// split of a power k into sweeps, Sec. 5.1), measured on the GPU.  A
+// candidate with sweeps of q < k powers is one plan with mpk_opts.sweep = q
+// (all sweeps in one launch), except on the resident schedule, which runs
+// one plan per sweep.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -90,31 +93,41 @@ int mpk_autotune(const mpk_csr *A, int32_t k, const mpk_opts *base, double min_t
     *best = -1;
     const size_t eb = is_f64_vec(base->prec) ? 8 : 4;
     const size_t vec = (size_t)A->n * (size_t)std::max(1, base->nrhs) * eb;
-    int32_t qmax = 1;
-    for (int32_t c = 0; c < n_cand; c++) qmax = std::max(qmax, std::min(std::max(1, cand[c].p_sweep), k));
     char *x = nullptr, *Y = nullptr;
     int rc = dev_alloc<char>(nullptr, &x, vec);
-    if (!rc) rc = dev_alloc<char>(nullptr, &Y, vec * (size_t)qmax);
+    if (!rc) rc = dev_alloc<char>(nullptr, &Y, vec * (size_t)k);
     if (!rc && cudaMemset(x, 0, vec) != cudaSuccess) rc = MPK_ERR_CUDA;
     double best_ms = INFINITY;
     for (int32_t c = 0; c < n_cand && !rc; c++) {
         mpk_tune_candidate &cd = cand[c];
-        const int32_t q = std::min(std::max(1, cd.p_sweep), k), sweeps = k / q, rem = k % q;
+        const int32_t q = std::min(std::max(1, cd.p_sweep), k);
         mpk_opts o = *base;
         o.tile_rows = cd.tile_rows;
         o.safety_f = cd.safety_f;
         o.tune = cd.tune;
         double ms = 0, t = 0;
         int st = MPK_OK;
-        for (int32_t part = 0; part < 2 && st == MPK_OK; part++) {
-            const int32_t pw = part == 0 ? q : rem;
-            const int32_t times = part == 0 ? sweeps : (rem ? 1 : 0);
-            if (!times) continue;
+        if (!(cd.tune & MPK_TUNE_RESIDENT)) {
+            // the work-list schedule runs the sweeps in one launch
+            o.sweep = q;
             mpk_plan_t plan = nullptr;
-            st = mpk_plan(A, pw, &o, &plan);
-            if (st == MPK_OK) st = time_plan(plan, x, Y, min_time_s, &t);
+            st = mpk_plan(A, k, &o, &plan);
+            if (st == MPK_OK) st = time_plan(plan, x, Y, min_time_s, &ms);
             if (plan) mpk_plan_destroy(plan);
-            ms += times * t;
+        } else {
+            // the resident schedule owns tiles for all powers of a launch:
+            // one launch per sweep, and one for the remainder
+            const int32_t sweeps = k / q, rem = k % q;
+            for (int32_t part = 0; part < 2 && st == MPK_OK; part++) {
+                const int32_t pw = part == 0 ? q : rem;
+                const int32_t times = part == 0 ? sweeps : (rem ? 1 : 0);
+                if (!times) continue;
+                mpk_plan_t plan = nullptr;
+                st = mpk_plan(A, pw, &o, &plan);
+                if (st == MPK_OK) st = time_plan(plan, x, Y, min_time_s, &t);
+                if (plan) mpk_plan_destroy(plan);
+                ms += times * t;
+            }
         }
         cd.status = st;
         cd.ms = st == MPK_OK ? ms : -1.0;

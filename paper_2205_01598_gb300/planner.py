@@ -11,10 +11,17 @@ autotuner (mpk_autotune) measured on generated matrices.  The autotuner is
 the fallback (no weights, or a predicted configuration that fails) and the
 yardstick of regret, regret = t(chosen) / t(best) - 1.
 
+A candidate's sweep length for k = 8 powers carries over to an MPK of p
+powers by its kind: one sweep of all powers, two sweeps (ceil(p/2)), or
+single-power sweeps (member_options); the batch takes each member's options
+that way.
+
 Command line (GPU):
-  python -m paper_2205_01598_gb300.planner collect --first 7000 --count 300 --out data.npz
-  python -m paper_2205_01598_gb300.planner train --data data.npz --out planner_weights.npz
+  python -m paper_2205_01598_gb300.planner collect --first 10000 --count 2000 --out train.npz
+  python -m paper_2205_01598_gb300.planner train --data train.npz --data train_large.npz --out planner_weights.npz
   python -m paper_2205_01598_gb300.planner evaluate --data heldout.npz --weights planner_weights.npz
+  python -m paper_2205_01598_gb300.planner record --data heldout.npz --data heldout_large.npz --headline \
+      --out planner_eval.json
 """
 from __future__ import annotations
 
@@ -26,14 +33,14 @@ import time
 
 import numpy as np
 
-from . import Mlp, csr_to_device, mpk_autotune, mpk_plan, mpk_plan_features, mpk_tune_default_grid
+from . import MPK_TUNE_RESIDENT, Mlp, csr_to_device, mpk_autotune, mpk_plan, mpk_plan_features, mpk_tune_default_grid
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "planner_weights.npz")
 K_POWERS = 8            # the MPK the planner is trained for
 HIDDEN = 64
 FAMILIES = ("laplace2d", "laplace3d", "box27", "rgg", "zipf")
-N_LO, N_HI = 10_000, 500_000
+N_LO, N_HI = 10_000, 2_000_000
 
 
 # ---------------------------------------------------------------- corpus
@@ -61,17 +68,34 @@ def corpus_matrix(i: int, n_lo: int = N_LO, n_hi: int = N_HI):
     return mi.zipf_graph(n, i)
 
 
+def headline_matrix(name: str):
+    """The two headline workloads as planner test matrices: the 3D 7-point
+    Laplacian on 160^3 and the 3D Anderson Hamiltonian on 200^3 (W = 16.5,
+    seed 42)."""
+    import mpk_inputs as mi
+    if name == "laplace3d-160":
+        return mi.laplace3d(160)
+    if name == "anderson3d-200":
+        return mi.anderson3d(200, W=16.5, seed=42)
+    raise ValueError(name)
+
+
+HEADLINE = ("laplace3d-160", "anderson3d-200")
+
+
 def _corpus_worker(args):
     i, n_lo, n_hi = args
     return corpus_matrix(i, n_lo, n_hi)
 
 
-def corpus(indices, n_lo=N_LO, n_hi=N_HI, workers=None, chunk=32):
+def corpus(indices, n_lo=N_LO, n_hi=N_HI, workers=None, chunk=None):
     """Yields (i, matrix) over `indices`, built on the host cores by a spawned
-    pool one chunk ahead of the consumer (bounded host memory)."""
+    pool one chunk ahead of the consumer (bounded host memory: chunks of 32
+    matrices up to 2M rows, 8 above)."""
     import multiprocessing as mp
     indices = list(indices)
-    workers = workers or min(16, os.cpu_count() or 1)
+    chunk = chunk or (32 if n_hi <= 2_000_000 else 8)
+    workers = workers or min(16 if n_hi <= 2_000_000 else 8, os.cpu_count() or 1)
     chunks = [indices[s:s + chunk] for s in range(0, len(indices), chunk)]
     with mp.get_context("spawn").Pool(workers) as pool:
         submit = lambda c: pool.map_async(_corpus_worker, [(i, n_lo, n_hi) for i in c])
@@ -193,54 +217,130 @@ def evaluate(planner, F, MS):
             "within_10pct_mlp": float(np.mean(r_mlp <= 0.10)), "within_10pct_default": float(np.mean(r_def <= 0.10))}
 
 
-def plan_options(rowptr, col, val, prec="f32", planner=None, use_weights=True):
-    """Options for the MPK of a matrix: the network's choice, or the
-    autotuner's when there is no network or the choice fails to plan."""
-    g = grid()
+def member_options(entry, p, k=K_POWERS):
+    """mpk_plan options for p powers from a grid entry tuned for k: the sweep
+    kind carries over (all k powers -> all p, ceil(k/2) -> ceil(p/2), one ->
+    one)."""
+    q = int(entry["p_sweep"])
+    sweep = p if q >= k else (1 if q == 1 else (p + 1) // 2)
+    return {"tile_rows": int(entry["tile_rows"]), "safety_f": float(entry["safety_f"]),
+            "tune": int(entry.get("tune", 0)), "sweep": sweep}
+
+
+def plan_options(rowptr, col, val, p=K_POWERS, prec="f32", nrhs=1, planner=None, use_weights=True, features=None):
+    """Options for the MPK of a matrix with p powers: the network's choice,
+    or the autotuner's (searched for p powers) when there is no network or
+    the choice fails to plan.  Returns a dict of mpk_plan keyword options
+    plus "source" and "grid_index"."""
     if planner is None and use_weights and os.path.exists(WEIGHTS):
         planner = Planner.load()
     if planner is not None:
-        probe = mpk_plan(rowptr, col, val, K_POWERS, prec=prec)
-        i = int(planner.choose(mpk_plan_features(probe))[0])
-        del probe
+        if features is None:
+            probe = mpk_plan(rowptr, col, val, K_POWERS, prec=prec)
+            features = mpk_plan_features(probe)
+            del probe
+        g = grid()
+        i = int(planner.choose(features)[0])
         if 0 <= i < len(g):
-            c = g[i]
+            o = member_options(g[i], p)
             try:
-                mpk_plan(rowptr, col, val, c["p_sweep"], prec=prec, tile_rows=c["tile_rows"],
-                         safety_f=c["safety_f"], tune=c.get("tune", 0))
-                return dict(c, source="mlp")
+                mpk_plan(rowptr, col, val, p, prec=prec, nrhs=nrhs, **o)
+                return dict(o, source="mlp", grid_index=i)
             except RuntimeError:
                 pass
-    best, _ = mpk_autotune(rowptr, col, val, K_POWERS, g, prec=prec)
-    return dict(g[best], source="autotuner")
+    g = mpk_tune_default_grid(p)
+    best, _ = mpk_autotune(rowptr, col, val, p, g, prec=prec, nrhs=nrhs, min_time_s=0.01)
+    return dict(member_options(g[best], p, p), source="autotuner", grid_index=best)
+
+
+def load_sets(paths):
+    """Concatenated features, timings and names of one or more collected sets."""
+    F, MS, names = [], [], []
+    for path in paths:
+        d = np.load(path)
+        F.append(d["features"])
+        MS.append(d["ms"])
+        names += [str(x) for x in d["names"]]
+    return np.concatenate(F), np.concatenate(MS), names
+
+
+def record(planner, paths, headline=False, min_time_s=0.01):
+    """Evaluation record of the planner: regret on the held-out sets and,
+    with headline=True, on the two headline matrices (measured here), per
+    matrix and in summary, split at N = 2M."""
+    F, MS, names = load_sets(paths)
+    if headline:
+        for name in HEADLINE:
+            f, ms, _ = measure(headline_matrix(name), min_time_s=min_time_s)
+            F = np.concatenate([F, f[None, :].astype(np.float32)])
+            MS = np.concatenate([MS, ms[None, :]])
+            names.append(f"{name}-headline")
+    choice = planner.choose(F)
+    r_mlp = regret(MS, choice)
+    r_def = regret(MS, np.full(MS.shape[0], default_index()))
+    best_fixed = int(np.argmin(regret_matrix(MS).mean(0)))
+    r_fix = regret(MS, np.full(MS.shape[0], best_fixed))
+    n = np.array([int(10 ** float(f[0]) + 0.5) for f in F])
+    rows = [{"matrix": nm, "n": int(nn), "best_ms": float(np.where(m > 0, m, np.inf).min()),
+             "chosen": int(c), "chosen_ms": float(m[c]), "regret": float(r)}
+            for nm, nn, m, c, r in zip(names, n, MS, choice, r_mlp)]
+
+    def summary(mask):
+        if not np.any(mask):
+            return None
+        return {"matrices": int(mask.sum()), "regret_mlp_mean": float(r_mlp[mask].mean()),
+                "regret_mlp_median": float(np.median(r_mlp[mask])),
+                "within_10pct_mlp": float(np.mean(r_mlp[mask] <= 0.10)),
+                "regret_best_fixed_entry_mean": float(r_fix[mask].mean()),
+                "regret_default_mean": float(r_def[mask].mean())}
+
+    return {"grid": grid(), "best_fixed_entry": best_fixed, "data": [os.path.basename(p) for p in paths],
+            "all": summary(np.ones(len(n), bool)), "n_up_to_2M": summary(n <= 2_000_000),
+            "n_above_2M": summary(n > 2_000_000), "matrices": rows}
+
+
+def regret_matrix(ms):
+    """Regret of every grid entry on every matrix (failed entries: the worst)."""
+    return np.stack([regret(ms, np.full(ms.shape[0], j)) for j in range(ms.shape[1])], 1)
 
 
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     c = sub.add_parser("collect")
-    c.add_argument("--first", type=int, default=7000)
-    c.add_argument("--count", type=int, default=300)
+    c.add_argument("--first", type=int, default=10000)
+    c.add_argument("--count", type=int, default=2000)
+    c.add_argument("--n-lo", type=int, default=N_LO)
     c.add_argument("--n-hi", type=int, default=N_HI)
     c.add_argument("--out", required=True)
     t = sub.add_parser("train")
-    t.add_argument("--data", required=True)
+    t.add_argument("--data", required=True, action="append")
     t.add_argument("--out", default=WEIGHTS)
-    t.add_argument("--epochs", type=int, default=3000)
+    t.add_argument("--epochs", type=int, default=4000)
     e = sub.add_parser("evaluate")
-    e.add_argument("--data", required=True)
+    e.add_argument("--data", required=True, action="append")
     e.add_argument("--weights", default=WEIGHTS)
+    r = sub.add_parser("record")
+    r.add_argument("--data", required=True, action="append")
+    r.add_argument("--weights", default=WEIGHTS)
+    r.add_argument("--headline", action="store_true")
+    r.add_argument("--out", required=True)
     a = ap.parse_args()
     if a.cmd == "collect":
-        collect(a.first, a.count, a.out, n_hi=a.n_hi)
+        collect(a.first, a.count, a.out, n_lo=a.n_lo, n_hi=a.n_hi)
     elif a.cmd == "train":
-        d = np.load(a.data)
-        planner, hist = train(d["features"], d["ms"], epochs=a.epochs)
+        F, MS, _ = load_sets(a.data)
+        planner, hist = train(F, MS, epochs=a.epochs)
         planner.save(a.out)
-        print(json.dumps({"train": evaluate(planner, d["features"], d["ms"]), "loss": hist[::5]}))
+        print(json.dumps({"train": evaluate(planner, F, MS), "loss": hist[::5]}))
+    elif a.cmd == "evaluate":
+        F, MS, _ = load_sets(a.data)
+        print(json.dumps(evaluate(Planner.load(a.weights), F, MS)))
     else:
-        d = np.load(a.data)
-        print(json.dumps(evaluate(Planner.load(a.weights), d["features"], d["ms"])))
+        rec = record(Planner.load(a.weights), a.data, headline=a.headline)
+        with open(a.out, "w") as f:
+            json.dump(rec, f, indent=1)
+        print(json.dumps({k: rec[k] for k in ("all", "n_up_to_2M", "n_above_2M")}))
 
 
 if __name__ == "__main__":

@@ -47,3 +47,34 @@ def test_product_path_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(root, f)).read()
                 assert "import oracle" not in src and "oracle/" not in src and "mpk_oracle" not in src, f
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structures have the C header's sizes and field
+    offsets (compiled with the host C compiler), so appended fields such as
+    mpk_opts.sweep land where the library reads them."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no host C compiler")
+    structs = {"mpk_opts": mpk.mpk_opts, "mpk_plan_stats": mpk.mpk_plan_stats,
+               "mpk_tune_candidate": mpk.mpk_tune_candidate}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{mpk.HEADER}"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                          text=True).stdout.split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(out[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"

@@ -78,13 +78,15 @@ def test_autotune_table(lib):
 
 
 def test_autotune_split_runs_remainder(lib):
-    """A split k = q*p + r times both plans; a candidate with p_sweep > k is
-    clamped to k."""
+    """Sweeps of 3 for k = 7 run as one plan (sweeps 3, 3, 1 in one launch);
+    a candidate with p_sweep > k is clamped to k; a resident candidate with
+    p_sweep < k times one plan per sweep and one for the remainder."""
     from paper_2205_01598_gb300 import csr_to_device, mpk_autotune
     A = mi.laplace2d(40)
-    cands = [{"tile_rows": 64, "safety_f": 0.5, "p_sweep": 3}, {"tile_rows": 64, "safety_f": 0.5, "p_sweep": 99}]
+    cands = [{"tile_rows": 64, "safety_f": 0.5, "p_sweep": 3}, {"tile_rows": 64, "safety_f": 0.5, "p_sweep": 99},
+             {"tile_rows": 0, "safety_f": 0.5, "p_sweep": 3, "tune": 8}]
     best, ms = mpk_autotune(*csr_to_device(A), 7, cands, prec="f64", min_time_s=0.002)
-    assert all(t > 0 for t in ms) and best in (0, 1)
+    assert all(t > 0 for t in ms) and best in (0, 1, 2)
 
 
 def test_planner_beats_default(lib):
@@ -116,11 +118,15 @@ def test_plan_options_network_and_fallbacks(lib):
     A = mi.laplace3d(30)
     rp, cl, va = csr_to_device(A)
     g = P.grid()
+    keys = ("tile_rows", "safety_f", "tune", "sweep")
     if os.path.exists(P.WEIGHTS):
         opt = P.plan_options(rp, cl, va)
-        assert opt["source"] == "mlp" and {k: opt[k] for k in g[0]} in g
-    opt = P.plan_options(rp, cl, va, use_weights=False)
-    assert opt["source"] == "autotuner" and {k: opt[k] for k in g[0]} in g
+        assert opt["source"] == "mlp" and {k: opt[k] for k in keys} == P.member_options(g[opt["grid_index"]], 8)
+        opt = P.plan_options(rp, cl, va, p=5, nrhs=3)      # a member of another p and width
+        assert {k: opt[k] for k in keys} == P.member_options(g[opt["grid_index"]], 5)
+    opt = P.plan_options(rp, cl, va, p=6, use_weights=False)
+    g6 = P.mpk_tune_default_grid(6)
+    assert opt["source"] == "autotuner" and {k: opt[k] for k in keys} == P.member_options(g6[opt["grid_index"]], 6, 6)
 
     class Broken:
         def choose(self, feats):

@@ -68,3 +68,31 @@ def test_schedule_is_complete_and_dependency_ordered(name, p):
     for j in range(T * p):
         if k[j] > 1:
             assert pos[lo[t[j]]:hi[t[j]] + 1, k[j] - 1].max() < j
+
+
+@pytest.mark.parametrize("name", ["laplace3d-30", "zipf-8000", "box27-12"])
+@pytest.mark.parametrize("p,q", [(8, 1), (8, 3), (10, 5), (7, 4)])
+def test_sweeps_in_one_launch_are_ordered_by_sweep(name, p, q):
+    """mpk_opts.sweep = q: every item of sweep s (powers s*q+1 .. (s+1)*q)
+    is issued after every item of sweep s-1, each dependency still earlier,
+    and the level groups are those of Eq. 5 for q powers (a plan for p = q
+    has the same groups)."""
+    make, kw = CASES[name]
+    A = make()
+    plan = plan_of(A, p, prec="f64", sweep=q, **kw)
+    info = mpk.mpk_plan_info(plan)
+    assert info["sweep"] == q and info["resident"] == 0
+    work, lo, hi = mpk.mpk_plan_schedule(plan)
+    T = info["n_tiles"]
+    t, k = work >> 8, work & 255
+    assert work.shape == (T * p,)
+    s = (k - 1) // q
+    assert np.all(np.diff(s) >= 0)
+    pos = np.empty((T, p + 1), dtype=np.int64)
+    pos[t, k] = np.arange(T * p)
+    for j in range(T * p):
+        if k[j] > 1:
+            assert pos[lo[t[j]]:hi[t[j]] + 1, k[j] - 1].max() < j
+    gp = mpk.mpk_plan_perm(plan)[2].cpu().numpy()
+    gq = mpk.mpk_plan_perm(plan_of(A, q, prec="f64", **kw))[2].cpu().numpy()
+    assert np.array_equal(gp, gq)
