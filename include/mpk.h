@@ -173,7 +173,7 @@ typedef struct {
     int64_t packed_entries;/* stored entries incl. padding of the packed layout  */
     int64_t matrix_bytes;  /* device bytes of the packed matrix (values+indices) */
     int64_t device_bytes;  /* all device memory held by the plan                 */
-    double plan_ms;        /* wall time of mpk_plan                              */
+    double plan_ms;        /* wall time of mpk_plan (phases in phase_ms)         */
     double cache_bytes;    /* C actually used in Eq. 5                           */
     double slope;          /* sigma: level groups between consecutive power fronts */
     int32_t staged;        /* 1 if work items stage their slice in shared memory */
@@ -183,6 +183,16 @@ typedef struct {
     int32_t dep_span;      /* widest forward dependency span, in tiles          */
     int32_t rec_stages;    /* recursion stages that refined something (Sec. 4.4) */
     int32_t sweep;         /* powers per sweep of the issue order (q <= p)       */
+    double phase_ms[8];    /* wall time of mpk_plan by phase (sum = plan_ms):
+                              [0] device attributes and CRS validation,
+                              [1] transposed pattern and BFS levels,
+                              [2] renumbering, P A P^T and row statistics,
+                              [3] level sizes and precision checks,
+                              [4] level groups (Eq. 5) and recursion,
+                              [5] work items, packing, dependency ranges,
+                              [6] grid size and issue order,
+                              [7] flags, the last synchronisation and the
+                                  release of temporary device memory        */
 } mpk_plan_stats;
 
 typedef struct mpk_plan_s *mpk_plan_t;

@@ -34,6 +34,9 @@ MPK_OK, MPK_ERR_INVALID, MPK_ERR_CUDA, MPK_ERR_OOM, MPK_ERR_TIMEOUT, MPK_ERR_UNS
 MPK_F64, MPK_F32, MPK_F32_BF16VAL, MPK_F64_DF = 0, 1, 2, 3
 MPK_IO_PERMUTED, MPK_ASYNC, MPK_SWEEP_ONE = 1, 2, 4
 MPK_TUNE_STAGE, MPK_TUNE_EVICT_LAST, MPK_TUNE_NO_SORT, MPK_TUNE_RESIDENT = 1, 2, 4, 8
+PLAN_PHASES = ("attributes+validation", "bfs_levels", "renumber+permute", "level_sizes+precision",
+               "groups+recursion", "tiles+pack+deps", "grid+issue_order", "flags+release")
+
 PRECISIONS = {"f64": MPK_F64, "f32": MPK_F32, "bf16val": MPK_F32_BF16VAL, "f64df": MPK_F64_DF}
 
 
@@ -96,7 +99,7 @@ class mpk_plan_stats(C.Structure):
                 ("cache_bytes", C.c_double), ("slope", C.c_double), ("staged", C.c_int32),
                 ("smem_bytes", C.c_int32), ("sorted", C.c_int32), ("resident", C.c_int32),
                 ("dep_span", C.c_int32), ("rec_stages", C.c_int32),
-                ("sweep", C.c_int32)]
+                ("sweep", C.c_int32), ("phase_ms", C.c_double * 8)]
 
 
 _lib = None
@@ -307,7 +310,9 @@ def mpk_autotune(rowptr, col, val, k, candidates, *, prec="f64", nrhs=1, min_tim
 def mpk_plan_info(plan: Plan) -> dict:
     s = mpk_plan_stats()
     _check(load().mpk_plan_info(plan.handle, C.byref(s)), "mpk_plan_info")
-    return {name: getattr(s, name) for name, _ in mpk_plan_stats._fields_}
+    out = {name: getattr(s, name) for name, _ in mpk_plan_stats._fields_}
+    out["phase_ms"] = list(out["phase_ms"])
+    return out
 
 
 def mpk_plan_features(plan: Plan) -> np.ndarray:

@@ -245,13 +245,45 @@ struct FlagProbe {
     }
 };
 
-// Bounded check for a range wider than one probe (huge levels, small tiles).
+// Check of a range wider than one probe (huge levels, small tiles): blocks
+// of kFlagBlock tiles that lie inside [lo, hi] by their counters of finished
+// tiles (a full count means every flag of the block holds this launch's
+// epoch: counters are zeroed at the end of every launch), the ragged ends and
+// the block holding `skip` flag by flag.
 __device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch, int lane, int32_t skip = -1) {
     const uint32_t *f = a.flags + (int64_t)(k - 1) * a.fstride;
     const int32_t lo = __ldg(a.dep_lo + t), hi = __ldg(a.dep_hi + t);
+    const int32_t b0 = (lo + kFlagBlock - 1) / kFlagBlock, b1 = (hi + 1) / kFlagBlock;   // full blocks [b0, b1)
     bool ok = true;
-    for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
+    if (b0 >= b1) {
+        for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
+    } else {
+        const int32_t sb = skip >= 0 ? skip / kFlagBlock : -1;
+        for (int32_t i = lo + lane; i < b0 * kFlagBlock; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
+        for (int32_t i = b1 * kFlagBlock + lane; i <= hi; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
+        const uint32_t *cnt = a.bcnt + (int64_t)(k - 1) * a.bstride;
+        for (int32_t b = b0 + lane; b < b1; b += 32)
+            if (b != sb) ok &= (ld_relaxed_u32(cnt + b) == (uint32_t)kFlagBlock);
+        if (sb >= b0 && sb < b1)
+            for (int32_t i = sb * kFlagBlock + lane; i < (sb + 1) * kFlagBlock; i += 32)
+                ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
+    }
     return __all_sync(0xffffffffu, ok);
+}
+
+// Completion of item (t, k): its epoch flag, then one more finished tile in
+// its block (both with release semantics: the item's outputs are visible to
+// whoever observes either).
+__device__ __forceinline__ void publish_item(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch) {
+    st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bcnt + (int64_t)k * a.bstride + t / kFlagBlock)
+                 : "memory");
+}
+
+// Zeroes the block counters of a plan (one warp), for the next launch.
+__device__ __forceinline__ void clear_block_counts(const ExecArgs &a, int lane) {
+    const int64_t total = (int64_t)(a.p + 1) * a.bstride;
+    for (int64_t i = lane; i < total; i += 32) a.bcnt[i] = 0u;
 }
 
 __device__ void record_timeout(const ExecArgs &a, int32_t k, int32_t t) {
@@ -585,6 +617,7 @@ struct OnePlan {
     __device__ __forceinline__ const ExecArgs &args(int32_t) const { return a; }
     __device__ __forceinline__ uint32_t epoch_of(int32_t) const { return epoch; }
     __device__ __forceinline__ void publish_epochs() const { atomicExch(a.ctl + CTL_EPOCH, (int)epoch); }
+    __device__ __forceinline__ void clear_counts(int lane) const { clear_block_counts(a, lane); }
 };
 struct ManyPlans {
     const ExecArgs *table;      // per plan (device memory)
@@ -597,6 +630,9 @@ struct ManyPlans {
     __device__ __forceinline__ uint32_t epoch_of(int32_t m) const { return epochs[m]; }
     __device__ __forceinline__ void publish_epochs() const {
         for (int32_t m = 0; m < count; m++) atomicExch(plan_ctl[m] + CTL_EPOCH, (int)epochs[m]);
+    }
+    __device__ __forceinline__ void clear_counts(int lane) const {
+        for (int32_t m = 0; m < count; m++) clear_block_counts(table[m], lane);
     }
 };
 
@@ -741,11 +777,13 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             }
             named_sync(kBarDone, nthr);   // compute warps finished item j
             if (STAGED) consumed++;
+            bool published = false;
             auto publish = [&]() {
+                if (published) return;
+                published = true;
                 const ExecArgs &aj = src.args(m);
                 const int32_t t = wk >> 8, k = wk & 255;
-                if (lane == 0 && !(t == aj.drop_tile && k == aj.drop_k))
-                    st_release_u32(aj.flags + (int64_t)k * aj.fstride + t, src.epoch_of(m));
+                if (lane == 0 && !(t == aj.drop_tile && k == aj.drop_k)) publish_item(aj, t, k, src.epoch_of(m));
             };
             if (jn >= g.n_items) {
                 publish();
@@ -767,7 +805,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             __syncwarp();
             named_arrive(kBarReady, nthr);
             if (!ready) break;
-            publish();   // off the compute warps' critical path (a repeat store is harmless)
+            publish();   // off the compute warps' critical path (unless published above)
             j = jn;
             m = mn;
             i++;
@@ -778,10 +816,17 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             if (!mbar_wait(&mbar[q % nst], (uint32_t)((q / nst) & 1), g.timeout_ns) && lane == 0)
                 record_timeout(g, 0, -1);
         __syncwarp();
+        int done = 0;
         if (lane == 0) {
             __threadfence();
-            const int done = atomicAdd(g.ctl + CTL_FINISHED, 1);
-            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch(s), reset
+            done = atomicAdd(g.ctl + CTL_FINISHED, 1);
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done == (int)gridDim.x - 1) {   // last CTA: clear the block counts, publish the epoch(s), reset
+            fence_acq_rel_gpu();
+            src.clear_counts(lane);
+            __syncwarp();
+            if (lane == 0) {
                 atomicExch(g.ctl + CTL_FINISHED, 0);
                 atomicExch(g.ctl + CTL_ABORT, 0);
                 src.publish_epochs();
@@ -950,9 +995,11 @@ __device__ __forceinline__ void resident_loop(const ExecArgs &a, uint32_t epoch,
             }
             named_sync(kBarDone, nthr);   // compute warps finished (t, k)
             if (k == P) consumed[q & 1]++;
+            bool published = false;
             auto publish = [&]() {
-                if (lane == 0 && !(t == a.drop_tile && k == a.drop_k))
-                    st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
+                if (published) return;
+                published = true;
+                if (lane == 0 && !(t == a.drop_tile && k == a.drop_k)) publish_item(a, t, k, epoch);
             };
             if (!more) {
                 publish();
@@ -973,7 +1020,7 @@ __device__ __forceinline__ void resident_loop(const ExecArgs &a, uint32_t epoch,
             __syncwarp();
             named_arrive(kBarReady, nthr);
             if (!ready) break;
-            publish();   // off the compute warps' critical path (a repeat store is harmless)
+            publish();   // off the compute warps' critical path (unless published above)
             q = qn;
             k = kn;
             t = tn;
@@ -986,10 +1033,17 @@ __device__ __forceinline__ void resident_loop(const ExecArgs &a, uint32_t epoch,
                 consumed[st]++;
             }
         __syncwarp();
+        int done = 0;
         if (lane == 0) {
             __threadfence();
-            const int done = atomicAdd(a.ctl + CTL_FINISHED, 1);
-            if (done == (int)gridDim.x - 1) {   // last CTA: publish the epoch, reset
+            done = atomicAdd(a.ctl + CTL_FINISHED, 1);
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done == (int)gridDim.x - 1) {   // last CTA: clear the block counts, publish the epoch, reset
+            fence_acq_rel_gpu();
+            clear_block_counts(a, lane);
+            __syncwarp();
+            if (lane == 0) {
                 atomicExch(a.ctl + CTL_FINISHED, 0);
                 atomicExch(a.ctl + CTL_ABORT, 0);
                 atomicExch(a.ctl + CTL_EPOCH, (int)epoch);
@@ -1815,6 +1869,8 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.diag = pl->d_diag;
     a.flags = pl->d_flags;
     a.fstride = pl->fstride;
+    a.bcnt = pl->d_bcnt;
+    a.bstride = pl->bstride;
     a.ctl = pl->d_ctl;
     a.n_tiles = pl->n_tiles;
     a.n_items = pl->n_tiles * pl->p;

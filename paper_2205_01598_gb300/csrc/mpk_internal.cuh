@@ -33,6 +33,10 @@ constexpr int kSpmvThreads = 256;                        // baseline SpMV CTA
 constexpr int kResWarps = MPK_RES_WARPS;                 // compute warps of a resident-schedule CTA
 constexpr int kResThreads = (kResWarps + 1) * 32;
 constexpr int kMaxStages = 3;                            // shared-memory stages of the staged work-list form
+// A dependency range wider than a flag probe is checked by counters of
+// finished tiles per block of kFlagBlock tiles (each finished item adds one),
+// and flag by flag only at its ragged ends.
+constexpr int kFlagBlock = 128;
 
 // Control words of a plan (device int32 array).
 enum Ctl : int {
@@ -86,6 +90,7 @@ struct Plan {
     std::vector<int32_t> h_group_stage;              // recursion stage that made each group (Sec. 4.4)
     int32_t rec_stages = 0;                          // stages of recursion that refined something
     int32_t sweep = 0;                               // powers per sweep of the issue order (q of mpk_opts.sweep)
+    double phase_ms[8] = {};                         // wall time of planning by phase (mpk_plan_stats.phase_ms)
 
     // device arrays (plan-owned)
     int32_t *d_perm = nullptr, *d_iperm = nullptr, *d_level = nullptr;
@@ -102,6 +107,8 @@ struct Plan {
     float *d_diag = nullptr;           // diagonal (only with has_diag)
     double *d_gersh = nullptr;         // Gershgorin row bounds scratch (lazily)
     uint32_t *d_flags = nullptr;       // (p+1) rows of fstride completion epochs
+    uint32_t *d_bcnt = nullptr;        // (p+1) rows of bstride per-block completion counts (zero between launches)
+    int32_t bstride = 0;               // blocks of kFlagBlock tiles
     int32_t fstride = 0;               // flag row length: n_tiles rounded up to 4, plus 4
     int32_t *d_ctl = nullptr;          // CTL_WORDS control words
     void *d_io = nullptr;              // permuted copies for unpermuted I/O (lazily)
@@ -143,6 +150,8 @@ struct ExecArgs {
     int32_t stage_recs;          // chunk records one resident stage holds
     int32_t n_stages;            // stages of the staged work-list form
     float2 *shadow;              // MPK_F64_DF: 2 blocks of n double-float pairs, power k in block k mod 2
+    uint32_t *bcnt;              // finished tiles per block of kFlagBlock tiles, power k at bcnt + k * bstride
+    int32_t bstride;
 };
 
 // Chebyshev sweep parameters (one wavefront launch computes powers k0+1 .. k0+pw).

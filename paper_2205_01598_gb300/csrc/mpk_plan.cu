@@ -151,11 +151,21 @@ __global__ void k_fill_transpose(int32_t n, const int32_t *rp, const int32_t *co
 // ---------------------------------------------------------------- BFS (Eq. 3)
 struct BfsCtl {
     unsigned bar_count, bar_gen;
-    int cnt[3];      // frontier sizes, rotating by level mod 3
-    int found[3];    // restart search results, rotating by search round mod 3
+    int cnt[3];            // frontier sizes by grid-barrier round mod 3 (see k_bfs)
+    int found[3];          // restart search results, rotating by search round mod 3
     int nlevels;
     int err;
+    int narrow_L[3];       // after a turn of one-CTA levels: first level not yet expanded,
+    int narrow_start[3];   // and the queue offset of its frontier (by round mod 3)
 };
+
+constexpr int kBfsThreads = 1024;   // one CTA per SM
+constexpr int kBfsBatch = 8;        // neighbours a lane loads before it tests them
+// Levels whose frontier fits one CTA (one vertex per thread) are expanded by
+// CTA 0 alone, level after level with __syncthreads between them, while the
+// other CTAs wait at the next grid barrier; a turn ends after kBfsNarrowRun
+// levels, so that the waits of the others stay short.
+constexpr int kBfsNarrowRun = 512;
 
 // Grid-wide barrier of a cooperative launch with a bounded wait.
 __device__ bool grid_sync(BfsCtl *c, uint64_t timeout_ns) {
@@ -172,12 +182,12 @@ __device__ bool grid_sync(BfsCtl *c, uint64_t timeout_ns) {
             st_release_u32(&c->bar_gen, gen + 1);
         } else {
             uint64_t t0 = global_ns();
-            unsigned ns = 32;
+            unsigned ns = 16;
             while (ld_relaxed_u32(&c->bar_gen) == gen) {
                 if (ld_relaxed_s32(&c->err)) { ok = 0; break; }
                 if (global_ns() - t0 > timeout_ns) { atomicCAS(&c->err, 0, (int)MPK_ERR_TIMEOUT); ok = 0; break; }
                 __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                if (ns < 64) ns <<= 1;
             }
         }
         fence_acq_rel_gpu();
@@ -187,13 +197,82 @@ __device__ bool grid_sync(BfsCtl *c, uint64_t timeout_ns) {
     return s_ok != 0;
 }
 
+// Expands the frontier queue[start, end) of level L: warps warp0,
+// warp0 + nwarps, ... take 32 frontier vertices each; a lane loads up to
+// kBfsBatch neighbours, then tests them, then claims the unvisited ones with
+// a compare-and-swap (so the loads of a batch overlap), and the warp appends
+// its claims to the queue after end with one atomic add.
+__device__ __forceinline__ void bfs_expand(int64_t start, int64_t end, int64_t warp0, int64_t nwarps, int lane,
+                                           const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                           const int32_t *__restrict__ trp, const int32_t *__restrict__ tcol,
+                                           int32_t L, int32_t *level, int32_t *queue, int *next_cnt) {
+    for (int64_t base = start + warp0 * 32; base < end; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        const bool valid = i < end;
+        int32_t a0 = 0, da = 0, t0 = 0, dt = 0;
+        if (valid) {
+            const int32_t u = queue[i];
+            a0 = __ldg(rp + u);
+            da = __ldg(rp + u + 1) - a0;
+            if (trp) {
+                t0 = __ldg(trp + u);
+                dt = __ldg(trp + u + 1) - t0;
+            }
+        }
+        const int32_t deg = da + dt;
+        const int32_t maxdeg = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)deg);
+        for (int32_t j0 = 0; j0 < maxdeg; j0 += kBfsBatch) {
+            int32_t v[kBfsBatch];
+#pragma unroll
+            for (int b = 0; b < kBfsBatch; b++) {
+                const int32_t j = j0 + b;
+                v[b] = j < deg ? (j < da ? __ldg(col + a0 + j) : __ldg(tcol + t0 + (j - da))) : -1;
+            }
+            unsigned disc = 0;
+#pragma unroll
+            for (int b = 0; b < kBfsBatch; b++)
+                if (v[b] >= 0 && ld_relaxed_s32(&level[v[b]]) < 0) disc |= 1u << b;
+#pragma unroll
+            for (int b = 0; b < kBfsBatch; b++)
+                if (((disc >> b) & 1u) && atomicCAS(&level[v[b]], -1, L + 1) != -1) disc &= ~(1u << b);
+            const int mine = __popc(disc);
+            int incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            if (total == 0) continue;
+            int at = 0;
+            if (lane == 31) at = atomicAdd(next_cnt, total);
+            at = __shfl_sync(0xffffffffu, at, 31);
+            int64_t pos = end + at + (incl - mine);
+#pragma unroll
+            for (int b = 0; b < kBfsBatch; b++)
+                if ((disc >> b) & 1u) queue[pos++] = v[b];
+        }
+    }
+}
+
 // Level-synchronous top-down BFS over the pattern (and its transpose when
 // trp != null).  Levels are hop distances from the root; when a level comes
 // out empty while vertices remain, the lowest-numbered unvisited vertex
-// starts the next level.  level[] must be -1 on entry.
-__global__ void __launch_bounds__(512) k_bfs(int32_t n, const int32_t *rp, const int32_t *col,
-                                             const int32_t *trp, const int32_t *tcol, int32_t root,
-                                             int32_t *level, int32_t *queue, BfsCtl *c, uint64_t timeout_ns) {
+// starts the next level.  level[] must be -1 on entry.  The levels do not
+// depend on the order in which a level's vertices are queued or claimed.
+//
+// Rounds are the stretches between grid barriers (R counts the barriers
+// passed).  The frontier size every CTA reads after barrier R is cnt[R % 3];
+// during round R only cnt[(R+1) % 3] (the next size) and cnt[(R+2) % 3]
+// (cleared for round R+1) are written, so no CTA can overwrite a size
+// another CTA has yet to read.  A narrow frontier (at most one vertex per
+// thread of a CTA) is expanded by CTA 0 alone for up to kBfsNarrowRun levels
+// in one round, counting in shared memory; it hands the state on through the
+// round's slots.
+__global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *rp, const int32_t *col,
+                                                     const int32_t *trp, const int32_t *tcol, int32_t root,
+                                                     int32_t *level, int32_t *queue, BfsCtl *c, uint64_t timeout_ns) {
+    __shared__ int s_cnt[3];
     const int lane = threadIdx.x & 31;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gsize = (int64_t)gridDim.x * blockDim.x;
@@ -201,15 +280,17 @@ __global__ void __launch_bounds__(512) k_bfs(int32_t n, const int32_t *rp, const
     if (gtid == 0) {
         level[root] = 0;
         queue[0] = root;
-        c->cnt[0] = 1;
+        c->cnt[1] = 1;   // read after the first barrier (round 1)
+        c->cnt[2] = 0;
         c->found[0] = c->found[1] = c->found[2] = INT_MAX;
     }
     if (!grid_sync(c, timeout_ns)) return;
+    uint32_t R = 1;
     int32_t L = 0;
     int64_t start = 0, cursor = 0;
     int round = 0;
     for (;;) {
-        int32_t size = ld_relaxed_s32(&c->cnt[L % 3]);
+        int32_t size = ld_relaxed_s32(&c->cnt[R % 3]);
         if (size == 0) {   // component finished: restart at the lowest unvisited vertex
             int32_t f = INT_MAX;
             for (;;) {
@@ -218,6 +299,7 @@ __global__ void __launch_bounds__(512) k_bfs(int32_t n, const int32_t *rp, const
                 int64_t idx = cursor + gtid;
                 if (idx < n && ld_relaxed_s32(&level[idx]) < 0) atomicMin(&c->found[slot], (int)idx);
                 if (!grid_sync(c, timeout_ns)) return;
+                R++;
                 f = ld_relaxed_s32(&c->found[slot]);
                 round++;
                 if (f != INT_MAX) break;
@@ -229,48 +311,68 @@ __global__ void __launch_bounds__(512) k_bfs(int32_t n, const int32_t *rp, const
             if (gtid == 0) {
                 level[f] = L;
                 queue[start] = f;
-                c->cnt[L % 3] = 1;
+                atomicExch(&c->cnt[(R + 1) % 3], 1);
+                atomicExch(&c->cnt[(R + 2) % 3], 0);
             }
             if (!grid_sync(c, timeout_ns)) return;
+            R++;
             size = 1;
         }
-        if (gtid == 0) c->cnt[(L + 2) % 3] = 0;
-        int *next_cnt = &c->cnt[(L + 1) % 3];
-        const int64_t end = start + size;
-        for (int64_t base = start + gwarp * 32; base < end; base += nwarps * 32) {
-            int64_t i = base + lane;
-            bool valid = i < end;
-            int32_t u = valid ? queue[i] : 0;
-            int32_t a0 = 0, da = 0, t0 = 0, dt = 0;
-            if (valid) {
-                a0 = rp[u];
-                da = rp[u + 1] - a0;
-                if (trp) { t0 = trp[u]; dt = trp[u + 1] - t0; }
-            }
-            int32_t deg = da + dt;
-            int32_t maxdeg = __reduce_max_sync(0xffffffffu, (unsigned)deg);
-            for (int32_t j = 0; j < maxdeg; j++) {
-                bool disc = false;
-                int32_t v = 0;
-                if (j < deg) {
-                    v = j < da ? col[a0 + j] : tcol[t0 + (j - da)];
-                    if (ld_relaxed_s32(&level[v]) < 0) disc = atomicCAS(&level[v], -1, L + 1) == -1;
+        if (size <= kBfsThreads) {
+            // narrow levels: CTA 0 alone, __syncthreads between levels
+            if (blockIdx.x == 0) {
+                if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0;
+                __syncthreads();
+                int32_t l = L, sz = size;
+                int64_t s0 = start;
+                for (int run = 0; run < kBfsNarrowRun; run++) {
+                    // level l counts into s_cnt[run % 3]; s_cnt[(run + 1) % 3] is
+                    // cleared for the next level (its last reads were before the
+                    // previous __syncthreads)
+                    if (threadIdx.x == 0) s_cnt[(run + 1) % 3] = 0;
+                    const int64_t e = s0 + sz;
+                    bfs_expand(s0, e, threadIdx.x >> 5, blockDim.x >> 5, lane, rp, col, trp, tcol, l, level, queue,
+                               &s_cnt[run % 3]);
+                    __syncthreads();
+                    s0 = e;
+                    l++;
+                    sz = *(volatile int *)&s_cnt[run % 3];
+                    if (sz == 0 || sz > kBfsThreads) break;
                 }
-                unsigned m = __ballot_sync(0xffffffffu, disc);
-                if (m) {
-                    int leader = __ffs(m) - 1;
-                    int pos = 0;
-                    if (lane == leader) pos = atomicAdd(next_cnt, __popc(m));
-                    pos = __shfl_sync(0xffffffffu, pos, leader);
-                    if (disc) queue[end + pos + __popc(m & ((1u << lane) - 1u))] = v;
+                if (threadIdx.x == 0) {
+                    c->narrow_L[(R + 1) % 3] = l;
+                    c->narrow_start[(R + 1) % 3] = (int)s0;
+                    atomicExch(&c->cnt[(R + 1) % 3], sz);
+                    atomicExch(&c->cnt[(R + 2) % 3], 0);
                 }
             }
+            if (!grid_sync(c, timeout_ns)) return;
+            R++;
+            L = ld_relaxed_s32(&c->narrow_L[R % 3]);
+            start = ld_relaxed_s32(&c->narrow_start[R % 3]);
+            continue;
         }
+        if (gtid == 0) atomicExch(&c->cnt[(R + 2) % 3], 0);
+        bfs_expand(start, start + size, gwarp, nwarps, lane, rp, col, trp, tcol, L, level, queue,
+                   &c->cnt[(R + 1) % 3]);
         if (!grid_sync(c, timeout_ns)) return;
-        start = end;
+        R++;
+        start += size;
         L++;
     }
     if (gtid == 0) c->nlevels = L;
+}
+
+// Cooperative launch of k_bfs: one CTA per SM.
+int launch_bfs(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *trp, const int32_t *tcol, int32_t root,
+               int32_t *level, int32_t *queue, BfsCtl *c, uint64_t timeout_ns, int num_sms, cudaStream_t st) {
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, kBfsThreads, 0));
+    if (occ < 1) return MPK_ERR_CUDA;
+    void *args[] = {(void *)&n, (void *)&rp, (void *)&col, (void *)&trp, (void *)&tcol, (void *)&root,
+                    (void *)&level, (void *)&queue, (void *)&c, (void *)&timeout_ns};
+    MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(num_sms), dim3(kBfsThreads), args, 0, st));
+    return MPK_OK;
 }
 
 // ---------------------------------------------------------------- stable radix sort by level
@@ -657,7 +759,7 @@ struct Scratch {
 void free_plan(Plan *pl) {
     void *ps[] = {pl->d_perm, pl->d_iperm, pl->d_level, pl->d_level_ptr, pl->d_group_ptr, pl->d_chunk_row,
                   pl->d_chunk_off, pl->d_tile_chunk, pl->d_dep_lo, pl->d_dep_hi, pl->d_work, pl->d_pcol,
-                  pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_ctl, pl->d_io, pl->d_cheb,
+                  pl->d_pval, pl->d_diag, pl->d_gersh, pl->d_flags, pl->d_bcnt, pl->d_ctl, pl->d_io, pl->d_cheb,
                   pl->d_tile_off, pl->d_work_rem, pl->d_row_map, pl->d_chunk_rec, pl->d_shadow, pl->d_kry};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -732,10 +834,6 @@ static int refine_levels(Plan *pl, const mpk_csr *A, int32_t p, int32_t s_max, d
     MPK_TRY(S.alloc(&d_meta, 2 * (size_t)n + 2));
     MPK_TRY(S.alloc(&d_lp, (size_t)n + 1));
     MPK_TRY(S.alloc(&bc, 1));
-    int occ = 0;
-    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, 512, 0));
-    if (occ < 1) return MPK_ERR_CUDA;
-    const int bfs_grid = pl->num_sms * std::min(occ, 2);
     for (int32_t s = 0; s < s_max; s++) {
         const int32_t G = (int32_t)gp.size() - 1;
         auto bulky = [&](int32_t g) {
@@ -768,14 +866,7 @@ static int refine_levels(Plan *pl, const mpk_csr *A, int32_t p, int32_t s_max, d
         // Eq. 3 on it, rooted at compacted vertex 0 (the first run's first row)
         MPK_CUDA(cudaMemsetAsync(slev, 0xff, sizeof(int32_t) * (size_t)m, st));
         MPK_CUDA(cudaMemsetAsync(bc, 0, sizeof(BfsCtl), st));
-        {
-            const int32_t *no = nullptr;
-            int32_t root = 0, mm = m;
-            uint64_t tns = timeout_ns;
-            void *args[] = {(void *)&mm, (void *)&srow, (void *)&scol, (void *)&no, (void *)&no, (void *)&root,
-                            (void *)&slev, (void *)&queue, (void *)&bc, (void *)&tns};
-            MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(bfs_grid), dim3(512), args, 0, st));
-        }
+        MPK_TRY(launch_bfs(m, srow, scol, nullptr, nullptr, 0, slev, queue, bc, timeout_ns, pl->num_sms, st));
         BfsCtl h_bc;
         MPK_CUDA(cudaMemcpyAsync(&h_bc, bc, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st));
         MPK_CUDA(cudaStreamSynchronize(st));
@@ -867,9 +958,21 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     pl->safety_f = o->safety_f;
     pl->timeout_s = o->timeout_s > 0 ? o->timeout_s : 2.0;
     const uint64_t timeout_ns = (uint64_t)(pl->timeout_s * 1e9);
+    auto t_mark = t_start;
+    auto mark = [&](int phase) {
+        const auto now = std::chrono::steady_clock::now();
+        pl->phase_ms[phase] += std::chrono::duration<double, std::milli>(now - t_mark).count();
+        t_mark = now;
+    };
     MPK_CUDA(cudaGetDevice(&pl->device));
-    cudaDeviceProp prop;
-    MPK_CUDA(cudaGetDeviceProperties(&prop, pl->device));
+    struct {
+        int multiProcessorCount, l2CacheSize, sharedMemPerBlockOptin, sharedMemPerMultiprocessor;
+    } prop;   // the four attributes planning needs (a full property query costs milliseconds)
+    MPK_CUDA(cudaDeviceGetAttribute(&prop.multiProcessorCount, cudaDevAttrMultiProcessorCount, pl->device));
+    MPK_CUDA(cudaDeviceGetAttribute(&prop.l2CacheSize, cudaDevAttrL2CacheSize, pl->device));
+    MPK_CUDA(cudaDeviceGetAttribute(&prop.sharedMemPerBlockOptin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device));
+    MPK_CUDA(cudaDeviceGetAttribute(&prop.sharedMemPerMultiprocessor, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                    pl->device));
     pl->num_sms = prop.multiProcessorCount;
     pl->cache_bytes = o->cache_bytes > 0 ? o->cache_bytes : (double)prop.l2CacheSize;
     const int32_t n = A->n;
@@ -885,6 +988,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_CUDA(cudaMemcpyAsync(&h_bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MPK_CUDA(cudaStreamSynchronize(st));
     if (h_bad) return MPK_ERR_INVALID;
+    mark(0);
 
     // 2. transposed pattern when symmetry is not promised
     int32_t *d_trp = nullptr, *d_tcol = nullptr;
@@ -908,19 +1012,8 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_TRY(S.alloc(&d_bc, 1));
     MPK_CUDA(cudaMemsetAsync(pl->d_level, 0xff, sizeof(int32_t) * (size_t)n, st));
     MPK_CUDA(cudaMemsetAsync(d_bc, 0, sizeof(BfsCtl), st));
-    {
-        int occ = 0;
-        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, 512, 0));
-        if (occ < 1) return MPK_ERR_CUDA;
-        int grid = pl->num_sms * std::min(occ, 2);
-        int32_t root = (o->root >= 0 && o->root < n) ? o->root : 0;
-        const int32_t *rp = A->rowptr, *cl = A->col;
-        int32_t *lvl = pl->d_level;
-        uint64_t tns = timeout_ns;
-        void *args[] = {(void *)&n, (void *)&rp, (void *)&cl, (void *)&d_trp, (void *)&d_tcol, (void *)&root,
-                        (void *)&lvl, (void *)&d_queue, (void *)&d_bc, (void *)&tns};
-        MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(grid), dim3(512), args, 0, st));
-    }
+    MPK_TRY(launch_bfs(n, A->rowptr, A->col, d_trp, d_tcol, (o->root >= 0 && o->root < n) ? o->root : 0, pl->d_level,
+                       d_queue, d_bc, timeout_ns, pl->num_sms, st));
     BfsCtl h_bc;
     MPK_CUDA(cudaMemcpyAsync(&h_bc, d_bc, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st));
     MPK_CUDA(cudaStreamSynchronize(st));
@@ -928,6 +1021,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     const int32_t L = h_bc.nlevels;
     if (L < 1 || L > n) return MPK_ERR_CUDA;
     pl->n_levels = L;
+    mark(1);
 
     // 4. stable renumbering by (level, original index): LSD radix sort on levels
     int32_t *kA, *kB, *vA, *vB, *hist;
@@ -980,6 +1074,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         f[4] = (float)((double)h[3] / std::max(1.0, (double)h[0]) / N);   // mean |col-row| / N
         f[5] = (float)((double)h[4] / N);                                  // max |col-row| / N
     }
+    mark(2);
 
     // 6. level sizes to the host
     int64_t *d_lnnz;
@@ -1041,11 +1136,12 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         f[6] = (float)std::log10((double)L);
         f[7] = (float)((double)pl->max_level_rows / n);
         f[8] = (float)((double)n / L / std::max(1, pl->max_level_rows));   // mean / largest level size
-        for (int q = 0; q < 16; q++) {
-            const int32_t l0 = (int32_t)((int64_t)L * q / 16), l1 = (int32_t)((int64_t)L * (q + 1) / 16);
-            f[9 + q] = (float)((double)(pl->h_level_ptr[l1] - pl->h_level_ptr[l0]) / n);
+        for (int b = 0; b < 16; b++) {
+            const int32_t l0 = (int32_t)((int64_t)L * b / 16), l1 = (int32_t)((int64_t)L * (b + 1) / 16);
+            f[9 + b] = (float)((double)(pl->h_level_ptr[l1] - pl->h_level_ptr[l0]) / n);
         }
     }
+    mark(3);
 
     // 7. level groups (Eq. 5): add levels while (q+1) * weight(T) < f * C,
     //    q the powers of one sweep
@@ -1087,6 +1183,8 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
                                      cudaMemcpyHostToDevice, st));
         }
     }
+
+    mark(4);
 
     // 8. tiles (work items) inside groups, chunks of 32 rows inside tiles
     // Work items of 512 rows by default: small enough that the rows in flight
@@ -1240,6 +1338,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
             mx = std::max(mx, toff[t + 1] - toff[t]);
             mc = std::max(mc, tile_chunk[t + 1] - tile_chunk[t]);
         }
+        mark(5);
         pl->stage_entries = ((mx + kChunk - 1) / kChunk) * kChunk;
         pl->stage_recs = ((mc + 7) / 8) * 8;
         pl->tune = o->tune;
@@ -1317,15 +1416,18 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
         MPK_CUDA(cudaStreamSynchronize(st));
         pl->h_work = std::move(work);
     }
+    mark(6);
     pl->fstride = ((pl->n_tiles + 3) / 4) * 4 + 4;
     MPK_TRY(dev_alloc(pl, &pl->d_flags, (size_t)(p + 1) * pl->fstride));
+    pl->bstride = (pl->n_tiles + kFlagBlock - 1) / kFlagBlock;
+    MPK_TRY(dev_alloc(pl, &pl->d_bcnt, (size_t)(p + 1) * pl->bstride));
+    MPK_CUDA(cudaMemsetAsync(pl->d_bcnt, 0, sizeof(uint32_t) * (size_t)(p + 1) * pl->bstride, st));
     MPK_TRY(dev_alloc(pl, &pl->d_ctl, CTL_WORDS));
     MPK_CUDA(cudaMemsetAsync(pl->d_flags, 0, sizeof(uint32_t) * (size_t)(p + 1) * pl->fstride, st));
     MPK_CUDA(cudaMemsetAsync(pl->d_ctl, 0, sizeof(int32_t) * CTL_WORDS, st));
 
     MPK_CUDA(cudaStreamSynchronize(st));
     MPK_CUDA(cudaGetLastError());
-    pl->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return MPK_OK;
 }
 
@@ -1402,8 +1504,37 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
     items.reserve((size_t)T * p);
     double slope = sigma;
     if (pl->rec_stages == 0) {
-        for (int32_t k = 1; k <= p; k++)
-            for (int32_t t = 0; t < T; t++) items.push_back({(k - 1) / q, v[t] + sigma * ((k - 1) % q), k, t});
+        // v(t) increases with t, so each power's items are already in key
+        // order: a merge of the q lists of each sweep (a heap over powers)
+        // gives the order of a full sort by (key, k, t) in O(T p log q).
+        work.clear();
+        work.reserve((size_t)T * p);
+        struct Head { double key; int32_t k, t; };
+        auto later = [](const Head &a, const Head &b) {
+            if (a.key != b.key) return a.key > b.key;
+            if (a.k != b.k) return a.k > b.k;
+            return a.t > b.t;
+        };
+        std::vector<Head> heap;
+        for (int32_t k0 = 1; k0 <= p; k0 += q) {
+            const int32_t k1 = std::min(p, k0 + q - 1);
+            heap.clear();
+            if (T > 0)
+                for (int32_t k = k0; k <= k1; k++) heap.push_back({v[0] + sigma * (k - k0), k, 0});
+            std::make_heap(heap.begin(), heap.end(), later);
+            while (!heap.empty()) {
+                std::pop_heap(heap.begin(), heap.end(), later);
+                Head &h = heap.back();
+                work.push_back((h.t << 8) | h.k);
+                if (++h.t < T) {
+                    h.key = v[h.t] + sigma * (h.k - k0);
+                    std::push_heap(heap.begin(), heap.end(), later);
+                } else {
+                    heap.pop_back();
+                }
+            }
+        }
+        return slope;
     } else {
         // After recursion a tile next to a refined subgraph may read rows
         // spread over all its sub-levels: one slope for every tile would
@@ -1510,13 +1641,19 @@ int mpk_plan(const mpk_csr *A, int32_t p, const mpk_opts *o, mpk_plan_t *out) {
     if (o->sweep < 0 || o->sweep > kMaxP) return MPK_ERR_INVALID;
     mpk_plan_s *h = new (std::nothrow) mpk_plan_s();
     if (!h) return MPK_ERR_OOM;
-    int rc = build_plan(&h->pl, A, p, o);
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = build_plan(&h->pl, A, p, o);   // its temporary device memory is released on return
     if (rc != MPK_OK) {
         cudaStreamSynchronize((cudaStream_t)o->stream);
         free_plan(&h->pl);
         delete h;
         return rc;
     }
+    Plan &pl = h->pl;
+    pl.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    double rest = pl.plan_ms;
+    for (int i = 0; i < 7; i++) rest -= pl.phase_ms[i];
+    pl.phase_ms[7] = std::max(0.0, rest);
     *out = h;
     return MPK_OK;
 }
@@ -1557,6 +1694,7 @@ int mpk_plan_info(mpk_plan_t plan, mpk_plan_stats *s) {
     s->dep_span = pl.dep_span;
     s->rec_stages = pl.rec_stages;
     s->sweep = pl.sweep;
+    for (int i = 0; i < 8; i++) s->phase_ms[i] = pl.phase_ms[i];
     s->smem_bytes = (int32_t)pl.smem_bytes;
     return MPK_OK;
 }
@@ -1617,17 +1755,12 @@ int mpk_levels_noalloc(int32_t n, int64_t nnz, const int32_t *rowptr, const int3
     MPK_CUDA(cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MPK_CUDA(cudaStreamSynchronize(st));
     if (h_bad) return MPK_ERR_INVALID;
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     MPK_CUDA(cudaGetDevice(&dev));
     MPK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, 512, 0));
-    if (occ < 1) return MPK_ERR_CUDA;
-    int grid = sms * std::min(occ, 2);
-    const int32_t *no_trp = nullptr, *no_tcol = nullptr;
-    uint64_t tns = (uint64_t)((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
-    void *args[] = {(void *)&n, (void *)&rowptr, (void *)&col, (void *)&no_trp, (void *)&no_tcol, (void *)&root,
-                    (void *)&level, (void *)&queue, (void *)&ctl, (void *)&tns};
-    MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(grid), dim3(512), args, 0, st));
+    const uint64_t tns = (uint64_t)((timeout_s > 0 ? timeout_s : 2.0) * 1e9);
+    rc = launch_bfs(n, rowptr, col, nullptr, nullptr, root, level, queue, ctl, tns, sms, st);
+    if (rc) return rc;
     BfsCtl h_bc;
     MPK_CUDA(cudaMemcpyAsync(&h_bc, ctl, sizeof(BfsCtl), cudaMemcpyDeviceToHost, st));
     MPK_CUDA(cudaStreamSynchronize(st));

@@ -20,8 +20,8 @@ Command line (GPU):
   python -m paper_2205_01598_gb300.planner collect --first 10000 --count 2000 --out train.npz
   python -m paper_2205_01598_gb300.planner train --data train.npz --data train_large.npz --out planner_weights.npz
   python -m paper_2205_01598_gb300.planner evaluate --data heldout.npz --weights planner_weights.npz
-  python -m paper_2205_01598_gb300.planner record --data heldout.npz --data heldout_large.npz --headline \
-      --out planner_eval.json
+  python -m paper_2205_01598_gb300.planner collect-headline --out headline.npz
+  python -m paper_2205_01598_gb300.planner record --data heldout.npz --data heldout_large.npz --data headline.npz --out planner_eval.json
 """
 from __future__ import annotations
 
@@ -124,15 +124,16 @@ def measure(A, prec="f32", min_time_s=0.02):
 def collect(first, count, out, n_lo=N_LO, n_hi=N_HI, prec="f32", min_time_s=0.01):
     """Features and grid timings of corpus matrices first .. first+count-1,
     saved to `out` (npz)."""
-    F, MS, names = [], [], []
+    F, MS, names, ns = [], [], [], []
     t0 = time.time()
     for i, A in corpus(range(first, first + count), n_lo, n_hi):
         f, ms, _ = measure(A, prec=prec, min_time_s=min_time_s)
         F.append(f)
         MS.append(ms)
         names.append(f"{corpus_spec(i, n_lo, n_hi)[0]}-{A.n}")
+        ns.append(A.n)
     np.savez(out, features=np.array(F, dtype=np.float32), ms=np.array(MS), names=np.array(names),
-             grid=json.dumps(grid()), seconds=time.time() - t0)
+             n=np.array(ns, dtype=np.int64), grid=json.dumps(grid()), seconds=time.time() - t0)
     return out
 
 
@@ -264,23 +265,44 @@ def load_sets(paths):
     return np.concatenate(F), np.concatenate(MS), names
 
 
-def record(planner, paths, headline=False, min_time_s=0.01):
-    """Evaluation record of the planner: regret on the held-out sets and,
-    with headline=True, on the two headline matrices (measured here), per
-    matrix and in summary, split at N = 2M."""
+def collect_headline(out, min_time_s=0.01):
+    """Features and grid timings of the two headline matrices, saved to `out`
+    in the format of collect()."""
+    F, MS, names, ns = [], [], [], []
+    t0 = time.time()
+    for name in HEADLINE:
+        A = headline_matrix(name)
+        f, ms, _ = measure(A, min_time_s=min_time_s)
+        F.append(f)
+        MS.append(ms)
+        names.append(f"{name}-headline")
+        ns.append(A.n)
+    np.savez(out, features=np.array(F, dtype=np.float32), ms=np.array(MS), names=np.array(names),
+             n=np.array(ns, dtype=np.int64), grid=json.dumps(grid()), seconds=time.time() - t0)
+    return out
+
+
+def set_sizes(paths):
+    """Rows N of the matrices of collected sets (from the feature log10 N
+    where a set does not store them)."""
+    out = []
+    for path in paths:
+        d = np.load(path)
+        out.append(d["n"] if "n" in d.files else np.rint(10.0 ** d["features"][:, 0].astype(np.float64)))
+    return np.concatenate(out).astype(np.int64)
+
+
+def record(planner, paths):
+    """Evaluation record of the planner on collected sets (held-out corpus
+    matrices, the headline matrices): regret per matrix and in summary, split
+    at N = 2M."""
     F, MS, names = load_sets(paths)
-    if headline:
-        for name in HEADLINE:
-            f, ms, _ = measure(headline_matrix(name), min_time_s=min_time_s)
-            F = np.concatenate([F, f[None, :].astype(np.float32)])
-            MS = np.concatenate([MS, ms[None, :]])
-            names.append(f"{name}-headline")
     choice = planner.choose(F)
     r_mlp = regret(MS, choice)
     r_def = regret(MS, np.full(MS.shape[0], default_index()))
     best_fixed = int(np.argmin(regret_matrix(MS).mean(0)))
     r_fix = regret(MS, np.full(MS.shape[0], best_fixed))
-    n = np.array([int(10 ** float(f[0]) + 0.5) for f in F])
+    n = set_sizes(paths)
     rows = [{"matrix": nm, "n": int(nn), "best_ms": float(np.where(m > 0, m, np.inf).min()),
              "chosen": int(c), "chosen_ms": float(m[c]), "regret": float(r)}
             for nm, nn, m, c, r in zip(names, n, MS, choice, r_mlp)]
@@ -320,10 +342,11 @@ def main():
     e = sub.add_parser("evaluate")
     e.add_argument("--data", required=True, action="append")
     e.add_argument("--weights", default=WEIGHTS)
+    h = sub.add_parser("collect-headline")
+    h.add_argument("--out", required=True)
     r = sub.add_parser("record")
     r.add_argument("--data", required=True, action="append")
     r.add_argument("--weights", default=WEIGHTS)
-    r.add_argument("--headline", action="store_true")
     r.add_argument("--out", required=True)
     a = ap.parse_args()
     if a.cmd == "collect":
@@ -333,11 +356,13 @@ def main():
         planner, hist = train(F, MS, epochs=a.epochs)
         planner.save(a.out)
         print(json.dumps({"train": evaluate(planner, F, MS), "loss": hist[::5]}))
+    elif a.cmd == "collect-headline":
+        collect_headline(a.out)
     elif a.cmd == "evaluate":
         F, MS, _ = load_sets(a.data)
         print(json.dumps(evaluate(Planner.load(a.weights), F, MS)))
     else:
-        rec = record(Planner.load(a.weights), a.data, headline=a.headline)
+        rec = record(Planner.load(a.weights), a.data)
         with open(a.out, "w") as f:
             json.dump(rec, f, indent=1)
         print(json.dumps({k: rec[k] for k in ("all", "n_up_to_2M", "n_above_2M")}))
