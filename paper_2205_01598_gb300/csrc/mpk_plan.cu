@@ -150,7 +150,8 @@ __global__ void k_fill_transpose(int32_t n, const int32_t *rp, const int32_t *co
 
 // ---------------------------------------------------------------- BFS (Eq. 3)
 struct BfsCtl {
-    unsigned bar_count, bar_gen;
+    unsigned bar_count;    // arrivals at grid barriers (never reset within a launch)
+    unsigned unused;
     int cnt[3];            // frontier sizes by grid-barrier round mod 3 (see k_bfs)
     int found[3];          // restart search results, rotating by search round mod 3
     int nlevels;
@@ -167,30 +168,29 @@ constexpr int kBfsBatch = 8;        // neighbours a lane loads before it tests t
 // levels, so that the waits of the others stay short.
 constexpr int kBfsNarrowRun = 512;
 
-// Grid-wide barrier of a cooperative launch with a bounded wait.
-__device__ bool grid_sync(BfsCtl *c, uint64_t timeout_ns) {
+// Grid-wide barrier of a cooperative launch with a bounded wait.  The
+// arrival counter only grows: the b-th barrier of the launch is complete when
+// it reaches b * gridDim.x, so an arrival is one atomic add and nothing has to
+// be reset or released by the last CTA.  `b` counts the barriers every CTA
+// has called (all CTAs call them in the same sequence).
+__device__ bool grid_sync(BfsCtl *c, uint32_t &b, uint64_t timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
+    b++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_relaxed_u32(&c->bar_gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            st_release_u32(&c->bar_gen, gen + 1);
-        } else {
-            uint64_t t0 = global_ns();
-            unsigned ns = 16;
-            while (ld_relaxed_u32(&c->bar_gen) == gen) {
+        const uint32_t target = b * gridDim.x;
+        fence_acq_rel_gpu();   // this CTA's writes before the arrival
+        const uint32_t arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+        if ((int32_t)(arrived - target) < 0) {
+            const uint64_t t0 = global_ns();
+            while ((int32_t)(ld_relaxed_u32(&c->bar_count) - target) < 0) {
                 if (ld_relaxed_s32(&c->err)) { ok = 0; break; }
                 if (global_ns() - t0 > timeout_ns) { atomicCAS(&c->err, 0, (int)MPK_ERR_TIMEOUT); ok = 0; break; }
-                __nanosleep(ns);
-                if (ns < 64) ns <<= 1;
+                __nanosleep(32);
             }
         }
-        fence_acq_rel_gpu();
+        fence_acq_rel_gpu();   // the other CTAs' writes before this CTA's next reads
         s_ok = ok;
     }
     __syncthreads();
@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
         c->cnt[2] = 0;
         c->found[0] = c->found[1] = c->found[2] = INT_MAX;
     }
-    if (!grid_sync(c, timeout_ns)) return;
+    uint32_t nbar = 0;
+    if (!grid_sync(c, nbar, timeout_ns)) return;
     uint32_t R = 1;
     int32_t L = 0;
     int64_t start = 0, cursor = 0;
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
                 if (gtid == 0) c->found[(round + 1) % 3] = INT_MAX;
                 int64_t idx = cursor + gtid;
                 if (idx < n && ld_relaxed_s32(&level[idx]) < 0) atomicMin(&c->found[slot], (int)idx);
-                if (!grid_sync(c, timeout_ns)) return;
+                if (!grid_sync(c, nbar, timeout_ns)) return;
                 R++;
                 f = ld_relaxed_s32(&c->found[slot]);
                 round++;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
                 atomicExch(&c->cnt[(R + 1) % 3], 1);
                 atomicExch(&c->cnt[(R + 2) % 3], 0);
             }
-            if (!grid_sync(c, timeout_ns)) return;
+            if (!grid_sync(c, nbar, timeout_ns)) return;
             R++;
             size = 1;
         }
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
                     atomicExch(&c->cnt[(R + 2) % 3], 0);
                 }
             }
-            if (!grid_sync(c, timeout_ns)) return;
+            if (!grid_sync(c, nbar, timeout_ns)) return;
             R++;
             L = ld_relaxed_s32(&c->narrow_L[R % 3]);
             start = ld_relaxed_s32(&c->narrow_start[R % 3]);
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
         if (gtid == 0) atomicExch(&c->cnt[(R + 2) % 3], 0);
         bfs_expand(start, start + size, gwarp, nwarps, lane, rp, col, trp, tcol, L, level, queue,
                    &c->cnt[(R + 1) % 3]);
-        if (!grid_sync(c, timeout_ns)) return;
+        if (!grid_sync(c, nbar, timeout_ns)) return;
         R++;
         start += size;
         L++;
@@ -450,23 +451,64 @@ __global__ void k_perm_len(int32_t n, const int32_t *rp, const int32_t *perm, in
 }
 
 // Row r of P A P^T = old row perm[r], columns renumbered through iperm and
-// put in ascending order (insertion sort; rows are short).
+// put in ascending order (stable).  kPermGroup lanes share a row, so its
+// entries are read and written as contiguous runs: a row of at most
+// kPermGroup * kPermSlots entries is held in registers and every entry's
+// place is its rank among the row's entries (shuffles within the group);
+// longer rows fall back to an insertion sort by the group's first lane.
+constexpr int kPermGroup = 8, kPermSlots = 8;
 __global__ void k_perm_fill(int32_t n, const int32_t *rp, const int32_t *col, const double *val,
                             const int32_t *perm, const int32_t *iperm, const int32_t *prow,
                             int32_t *pcol, double *pval) {
-    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    int32_t o = perm[r], a = rp[o], len = rp[o + 1] - a, base = prow[r];
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = gid / kPermGroup;
+    const int sub = (int)(gid % kPermGroup), lane = threadIdx.x & 31;
+    const unsigned gmask = ((1u << kPermGroup) - 1u) << (lane & ~(kPermGroup - 1));
+    if (r >= n) return;   // whole groups (kPermGroup divides 32 and the block size)
+    const int32_t o = __ldg(perm + r), a = __ldg(rp + o), len = __ldg(rp + o + 1) - a, base = __ldg(prow + r);
+    if (len <= kPermGroup * kPermSlots) {
+        int32_t c[kPermSlots];
+#pragma unroll
+        for (int k = 0; k < kPermSlots; k++) {
+            const int32_t j = sub + k * kPermGroup;
+            c[k] = j < len ? __ldg(iperm + __ldg(col + a + j)) : INT_MAX;
+        }
+        int32_t rank[kPermSlots] = {};
+        const int32_t used = (len + kPermGroup - 1) / kPermGroup;   // slots in use (uniform in the group)
+#pragma unroll
+        for (int k2 = 0; k2 < kPermSlots; k2++) {
+            if (k2 >= used) break;   // uniform in the group
+            for (int q = 0; q < kPermGroup; q++) {
+                const int32_t cq = __shfl_sync(gmask, c[k2], q, kPermGroup);
+                const int32_t jq = q + k2 * kPermGroup;
+#pragma unroll
+                for (int k = 0; k < kPermSlots; k++) {
+                    const int32_t j = sub + k * kPermGroup;
+                    rank[k] += (cq < c[k]) || (cq == c[k] && jq < j);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPermSlots; k++) {
+            const int32_t j = sub + k * kPermGroup;
+            if (j < len) {
+                pcol[base + rank[k]] = c[k];
+                pval[base + rank[k]] = __ldg(val + a + j);
+            }
+        }
+        return;
+    }
+    if (sub != 0) return;
     for (int32_t j = 0; j < len; j++) {
-        int32_t c = iperm[col[a + j]];
+        int32_t cc = iperm[col[a + j]];
         double v = val[a + j];
         int32_t k = base + j;
-        while (k > base && pcol[k - 1] > c) {
+        while (k > base && pcol[k - 1] > cc) {
             pcol[k] = pcol[k - 1];
             pval[k] = pval[k - 1];
             k--;
         }
-        pcol[k] = c;
+        pcol[k] = cc;
         pval[k] = v;
     }
 }
@@ -642,20 +684,28 @@ __global__ void k_tile_of_row(int32_t n_tiles, const int32_t *tile_row, int32_t 
 // under transposition so that "t reads u" implies "u reads t".
 __global__ void k_deps(int32_t n, const int32_t *prow, const int32_t *pcol, const int32_t *tor, int symmetric,
                        int32_t *lo, int32_t *hi) {
-    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    int32_t t = tor[r], mn = t, mx = t;
-    for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
-        int32_t u = tor[pcol[e]];
-        mn = min(mn, u);
-        mx = max(mx, u);
-        if (!symmetric) {
-            atomicMin(&lo[u], t);
-            atomicMax(&hi[u], t);
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = r < n;
+    int32_t t = valid ? tor[r] : -1, mn = t, mx = t;
+    if (valid) {
+        for (int32_t e = prow[r]; e < prow[r + 1]; e++) {
+            int32_t u = tor[pcol[e]];
+            mn = min(mn, u);
+            mx = max(mx, u);
+            if (!symmetric) {
+                atomicMin(&lo[u], t);
+                atomicMax(&hi[u], t);
+            }
         }
     }
-    atomicMin(&lo[t], mn);
-    atomicMax(&hi[t], mx);
+    // the rows of a warp lie in one or two tiles: one atomic pair per tile
+    const unsigned same = __match_any_sync(0xffffffffu, t);
+    mn = __reduce_min_sync(same, mn);   // rows past n form their own group (t = -1)
+    mx = __reduce_max_sync(same, mx);
+    if (valid && (threadIdx.x & 31) == __ffs(same) - 1) {
+        atomicMin(&lo[t], mn);
+        atomicMax(&hi[t], mx);
+    }
 }
 
 __global__ void k_widen(int32_t n, const int32_t *a, int64_t *b) {
@@ -737,16 +787,37 @@ __global__ void k_apply_sub_order(int32_t m, const int32_t *ord, const int32_t *
     if (j < m) perm_out[comp_row[j]] = perm_in[comp_row[ord[j]]];
 }
 
+// Temporary device memory of one planning call: buffers are carved out of
+// slabs (256-byte aligned) and released together when planning returns, so
+// planning makes a few allocations instead of one per buffer.  The first slab
+// is sized by `hint`; a request that does not fit gets a slab of its own size.
 struct Scratch {
-    std::vector<void *> ptrs;
+    std::vector<void *> slabs;
+    char *cur = nullptr;
+    size_t left = 0, hint = 0;
     ~Scratch() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : slabs) cudaFree(p);
     }
     template <typename T>
     int alloc(T **p, size_t count) {
-        int rc = dev_alloc<T>(nullptr, p, count);
-        if (rc == MPK_OK) ptrs.push_back(*p);
-        return rc;
+        const size_t bytes = (std::max<size_t>(count, 1) * sizeof(T) + 255) & ~(size_t)255;
+        if (bytes > left) {
+            const size_t size = std::max(bytes, hint);
+            hint = 0;
+            char *q = nullptr;
+            const int rc = dev_alloc<char>(nullptr, &q, size);
+            if (rc != MPK_OK) {
+                *p = nullptr;
+                return rc;
+            }
+            slabs.push_back(q);
+            cur = q;
+            left = size;
+        }
+        *p = (T *)cur;
+        cur += bytes;
+        left -= bytes;
+        return MPK_OK;
     }
 };
 
@@ -798,7 +869,8 @@ static int permute_matrix(Plan *pl, const mpk_csr *A, int32_t *prow, int32_t *pl
     MPK_CUDA(cudaMemsetAsync(plen + n, 0, sizeof(int32_t), st));
     k_perm_len<<<blocks_for(n, 256), 256, 0, st>>>(n, A->rowptr, pl->d_perm, plen);
     MPK_TRY(exclusive_scan<int32_t>(plen, prow, (int64_t)n + 1, st, nullptr));
-    k_perm_fill<<<blocks_for(n, 128), 128, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm, pl->d_iperm, prow,
+    k_perm_fill<<<blocks_for((int64_t)n * kPermGroup, 256), 256, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm,
+                                                                          pl->d_iperm, prow,
                                                     pcol, pval);
     MPK_CUDA(cudaGetLastError());
     return MPK_OK;
@@ -978,6 +1050,10 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     const int32_t n = A->n;
     const int64_t nnz = A->nnz;
     Scratch S;
+    // what the buffers below take for n rows and nnz entries (transposed
+    // pattern included when symmetry is not promised)
+    S.hint = (size_t)(64 + (A->assume_symmetric ? 0 : 12)) * (size_t)A->n +
+             (size_t)(12 + (A->assume_symmetric ? 0 : 4)) * (size_t)A->nnz + ((size_t)1 << 20);
 
     // 1. validation of the CRS arrays on the device
     int32_t *d_bad;
@@ -1050,7 +1126,8 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_CUDA(cudaMemsetAsync(plen + n, 0, sizeof(int32_t), st));
     k_perm_len<<<blocks_for(n, 256), 256, 0, st>>>(n, A->rowptr, pl->d_perm, plen);
     MPK_TRY(exclusive_scan<int32_t>(plen, prow, (int64_t)n + 1, st, nullptr));
-    k_perm_fill<<<blocks_for(n, 128), 128, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm, pl->d_iperm, prow,
+    k_perm_fill<<<blocks_for((int64_t)n * kPermGroup, 256), 256, 0, st>>>(n, A->rowptr, A->col, A->val, pl->d_perm,
+                                                                          pl->d_iperm, prow,
                                                     pcol, pval);
 
     // features of the matrix for the learned planner (host array of the plan)
