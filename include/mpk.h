@@ -357,16 +357,16 @@ int mpk_cheb_real_host(mpk_plan_t plan, const double *coef, int32_t M, double c,
  * Several plans (different matrices, sizes, block widths nrhs and powers p)
  * run in ONE persistent wavefront launch: their issue orders (each the
  * diagonal order of its own Lp diagram, with the plan's own work-item size,
- * f and sweep length) follow one another, largest plan first, so every plan
- * keeps its dependency order, the drain of one plan overlaps the start of
- * the next, and the items of all plans share the CTAs of the GPU.  Plans must have the same precision (MPK_F64 or
+ * f and sweep length) are merged by relative position, so every plan keeps
+ * its dependency order, and the items of all plans share the CTAs of the
+ * GPU.  Plans must have the same precision (MPK_F64 or
  * MPK_F32; MPK_F32_BF16VAL is MPK_ERR_UNSUPPORTED) and device, and must not be
  * run on their own while the batch runs (they share their dependency flags).
  * The batch uses the stream of plans[0].  Vectors are in each plan's level
  * order (as with MPK_IO_PERMUTED).                                          */
 typedef struct mpk_batch_s *mpk_batch_t;
 
-/* Builds the joint issue order of `count` plans (host array of handles,
+/* Builds the merged issue order of `count` plans (host array of handles,
  * 1 <= count <= 1024; the batch keeps pointers to the plans, which must
  * outlive it).                                                            */
 int mpk_batch_create(const mpk_plan_t *plans, int32_t count, mpk_batch_t *out);

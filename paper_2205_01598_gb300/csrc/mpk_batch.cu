@@ -33,28 +33,31 @@ void free_batch(Batch *b) {
         if (p) cudaFree(p);
 }
 
-// Issue order of the batch: the plans' own orders one after another,
-// largest plan first (each plan keeps its order, so its dependencies stay
-// earlier).  CTAs that finish a plan's last items go straight on to the next
-// plan, so the drain of one plan overlaps the start of the next, and at any
-// time the L2 holds the level-group window of one or two plans: interleaving
-// all plans through the launch would make every plan's window compete for L2
-// at once.  The smallest plans come last, where the launch drains.
+// Issue order of the batch: the plans' own orders merged by relative
+// position (item j of a plan with n items sits at (j + 1/2) / n), so each
+// plan keeps its order (its dependencies stay earlier) and all plans advance
+// together through the launch: while one plan's items wait for the previous
+// power, the CTAs hold items of the others.  (Plans one after another, the
+// largest first, measured 213 vs 209 ms on the 64-matrix Zipf batch and
+// 322 vs 287 ms with the default options.)
 void merge_orders(const std::vector<Plan *> &plans, std::vector<int32_t> &work, std::vector<int32_t> &wplan) {
-    std::vector<int32_t> order(plans.size());
-    for (size_t m = 0; m < plans.size(); m++) order[m] = (int32_t)m;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return plans[a]->h_work.size() > plans[b]->h_work.size();
-    });
+    struct Ref { double pos; int32_t m, j; };
+    std::vector<Ref> refs;
     size_t total = 0;
     for (const Plan *pl : plans) total += pl->h_work.size();
-    work.clear();
-    wplan.clear();
-    work.reserve(total);
-    wplan.reserve(total);
-    for (int32_t m : order) {
-        work.insert(work.end(), plans[m]->h_work.begin(), plans[m]->h_work.end());
-        wplan.insert(wplan.end(), plans[m]->h_work.size(), m);
+    refs.reserve(total);
+    for (int32_t m = 0; m < (int32_t)plans.size(); m++) {
+        const double n = (double)plans[m]->h_work.size();
+        for (int32_t j = 0; j < (int32_t)plans[m]->h_work.size(); j++) refs.push_back({(j + 0.5) / n, m, j});
+    }
+    std::sort(refs.begin(), refs.end(), [](const Ref &a, const Ref &b) {
+        return a.pos != b.pos ? a.pos < b.pos : (a.m != b.m ? a.m < b.m : a.j < b.j);
+    });
+    work.resize(total);
+    wplan.resize(total);
+    for (size_t i = 0; i < total; i++) {
+        work[i] = plans[refs[i].m]->h_work[refs[i].j];
+        wplan[i] = refs[i].m;
     }
 }
 

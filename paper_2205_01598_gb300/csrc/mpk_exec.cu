@@ -208,6 +208,7 @@ __device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t *p) {
 // the check costs no round trip.  Flag rows are padded so that a 16-byte load
 // that starts at a multiple of 4 inside [lo, hi] stays in bounds.
 constexpr int kProbeVec = 2;   // 2 x 32 lanes x 4 flags = 256 flags per probe
+static_assert(kProbeVec * 128 == kProbeFlags, "probe width");
 
 struct FlagProbe {
     uint4 v[kProbeVec];
@@ -255,7 +256,7 @@ __device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epo
     const int32_t lo = __ldg(a.dep_lo + t), hi = __ldg(a.dep_hi + t);
     const int32_t b0 = (lo + kFlagBlock - 1) / kFlagBlock, b1 = (hi + 1) / kFlagBlock;   // full blocks [b0, b1)
     bool ok = true;
-    if (b0 >= b1) {
+    if (b0 >= b1 || !a.bcnt) {
         for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
     } else {
         const int32_t sb = skip >= 0 ? skip / kFlagBlock : -1;
@@ -271,17 +272,19 @@ __device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epo
     return __all_sync(0xffffffffu, ok);
 }
 
-// Completion of item (t, k): its epoch flag, then one more finished tile in
-// its block (both with release semantics: the item's outputs are visible to
-// whoever observes either).
+// Completion of item (t, k): its epoch flag, then, in plans with ranges wider
+// than a probe, one more finished tile in its block (both with release
+// semantics: the item's outputs are visible to whoever observes either).
 __device__ __forceinline__ void publish_item(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch) {
     st_release_u32(a.flags + (int64_t)k * a.fstride + t, epoch);
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bcnt + (int64_t)k * a.bstride + t / kFlagBlock)
-                 : "memory");
+    if (a.bcnt)
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bcnt + (int64_t)k * a.bstride + t / kFlagBlock)
+                     : "memory");
 }
 
 // Zeroes the block counters of a plan (one warp), for the next launch.
 __device__ __forceinline__ void clear_block_counts(const ExecArgs &a, int lane) {
+    if (!a.bcnt) return;
     const int64_t total = (int64_t)(a.p + 1) * a.bstride;
     for (int64_t i = lane; i < total; i += 32) a.bcnt[i] = 0u;
 }
@@ -1869,7 +1872,7 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y) {
     a.diag = pl->d_diag;
     a.flags = pl->d_flags;
     a.fstride = pl->fstride;
-    a.bcnt = pl->d_bcnt;
+    a.bcnt = pl->wide_deps ? pl->d_bcnt : nullptr;
     a.bstride = pl->bstride;
     a.ctl = pl->d_ctl;
     a.n_tiles = pl->n_tiles;

@@ -37,6 +37,9 @@ constexpr int kMaxStages = 3;                            // shared-memory stages
 // finished tiles per block of kFlagBlock tiles (each finished item adds one),
 // and flag by flag only at its ragged ends.
 constexpr int kFlagBlock = 128;
+// Widest dependency range (in flags, from its start rounded down to 4) that
+// one 16-byte-per-lane probe of a warp covers; wider ranges use the counters.
+constexpr int kProbeFlags = 256;
 
 // Control words of a plan (device int32 array).
 enum Ctl : int {
@@ -108,6 +111,7 @@ struct Plan {
     double *d_gersh = nullptr;         // Gershgorin row bounds scratch (lazily)
     uint32_t *d_flags = nullptr;       // (p+1) rows of fstride completion epochs
     uint32_t *d_bcnt = nullptr;        // (p+1) rows of bstride per-block completion counts (zero between launches)
+    int32_t wide_deps = 0;             // some tile's dependency range is wider than a probe (counters in use)
     int32_t bstride = 0;               // blocks of kFlagBlock tiles
     int32_t fstride = 0;               // flag row length: n_tiles rounded up to 4, plus 4
     int32_t *d_ctl = nullptr;          // CTL_WORDS control words
@@ -150,7 +154,8 @@ struct ExecArgs {
     int32_t stage_recs;          // chunk records one resident stage holds
     int32_t n_stages;            // stages of the staged work-list form
     float2 *shadow;              // MPK_F64_DF: 2 blocks of n double-float pairs, power k in block k mod 2
-    uint32_t *bcnt;              // finished tiles per block of kFlagBlock tiles, power k at bcnt + k * bstride
+    uint32_t *bcnt;              // finished tiles per block of kFlagBlock tiles, power k at bcnt + k * bstride;
+                                 // null when every dependency range fits a probe (no counting)
     int32_t bstride;
 };
 

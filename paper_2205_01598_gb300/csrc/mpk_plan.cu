@@ -1452,7 +1452,10 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     MPK_CUDA(cudaMemcpyAsync(pl->h_dep_hi.data(), pl->d_dep_hi, sizeof(int32_t) * pl->h_dep_hi.size(),
                              cudaMemcpyDeviceToHost, st));
     MPK_CUDA(cudaStreamSynchronize(st));
-    for (int32_t t = 0; t < pl->n_tiles; t++) pl->dep_span = std::max(pl->dep_span, pl->h_dep_hi[t] - t);
+    for (int32_t t = 0; t < pl->n_tiles; t++) {
+        pl->dep_span = std::max(pl->dep_span, pl->h_dep_hi[t] - t);
+        if (pl->h_dep_hi[t] - (pl->h_dep_lo[t] & ~3) >= kProbeFlags) pl->wide_deps = 1;
+    }
     if (pl->resident) {
         // resident schedule: res_per_sm CTAs per SM, each owning whole tiles;
         // the wait chains cannot close when G > (p-1) * span (or every tile
