@@ -762,8 +762,13 @@ def run_cheb(args, kind, size, p, prec, desc):
     sweeps = -(-CHEB_M // p)
     alg = sweeps * cheb_sweep_bytes(kind, A.nnz, A.n, prec, G)
     achieved = alg / (ms * 1e-3) / 1e9
+    # DRAM bytes of one sweep launch (one ncu capture of the same workload),
+    # while the kernel sources are those of the capture
+    traffic = recorded_traffic("k_cheb_wave_anderson200_m64.md", prec) if (kind, size) == ("anderson3d", 200) else None
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+            "traffic_unit": "DRAM bytes (read + write) per sweep launch",
+            "algorithmic_bytes_per_launch": int(alg / sweeps),
             "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
             "algorithmic_bytes_per_step": int(alg),
             "note": f"{sweeps} sweeps per step; per sweep the matrix once, two state vectors read and two "

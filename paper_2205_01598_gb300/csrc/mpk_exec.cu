@@ -251,12 +251,13 @@ struct FlagProbe {
 // tiles (a full count means every flag of the block holds this launch's
 // epoch: counters are zeroed at the end of every launch), the ragged ends and
 // the block holding `skip` flag by flag.
+template <bool COUNT = true>
 __device__ bool ready_wide(const ExecArgs &a, int32_t t, int32_t k, uint32_t epoch, int lane, int32_t skip = -1) {
     const uint32_t *f = a.flags + (int64_t)(k - 1) * a.fstride;
     const int32_t lo = __ldg(a.dep_lo + t), hi = __ldg(a.dep_hi + t);
     const int32_t b0 = (lo + kFlagBlock - 1) / kFlagBlock, b1 = (hi + 1) / kFlagBlock;   // full blocks [b0, b1)
     bool ok = true;
-    if (b0 >= b1 || !a.bcnt) {
+    if (!COUNT || b0 >= b1 || !a.bcnt) {
         for (int32_t i = lo + lane; i <= hi; i += 32) ok &= (i == skip || ld_relaxed_u32(f + i) == epoch);
     } else {
         const int32_t sb = skip >= 0 ? skip / kFlagBlock : -1;
@@ -300,10 +301,11 @@ __device__ void record_timeout(const ExecArgs &a, int32_t k, int32_t t) {
 // Polls until the item's dependencies are complete.  Bounded: after
 // timeout_ns it records MPK_ERR_TIMEOUT with the node, raises the abort word
 // and returns false; it also returns false once another CTA has aborted.
+template <bool COUNT = true>
 __device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k, uint32_t epoch, int lane,
                           int32_t skip = -1) {
     const bool wide = !pr.fits();
-    if (wide ? ready_wide(a, t, k, epoch, lane, skip) : pr.ready(epoch, lane, skip)) {
+    if (wide ? ready_wide<COUNT>(a, t, k, epoch, lane, skip) : pr.ready(epoch, lane, skip)) {
         fence_acq_rel_gpu();
         return true;
     }
@@ -323,7 +325,7 @@ __device__ bool wait_deps(const ExecArgs &a, FlagProbe &pr, int32_t t, int32_t k
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
         if (wide) {
-            if (ready_wide(a, t, k, epoch, lane, skip)) break;
+            if (ready_wide<COUNT>(a, t, k, epoch, lane, skip)) break;
         } else {
             pr.issue(a, t, k, lane);
             if (pr.ready(epoch, lane, skip)) break;
@@ -658,7 +660,9 @@ struct ManyPlans {
 // slice in registers (Slice): they know which item comes next because the
 // dealing is static -- the scheduler hands them items blockIdx.x,
 // blockIdx.x + gridDim.x, ... in that order, or -1 to stop.
-template <typename Node, typename MT, bool STAGED, typename Src, typename Extra, int PC = kPC>
+// COUNT: the completion counters may be in use (see ready_wide); without
+// it the plan's ranges all fit a probe and an item publishes its flag alone.
+template <typename Node, typename MT, bool STAGED, typename Src, typename Extra, int PC = kPC, bool COUNT = true>
 __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, const Extra &extra) {
     extern __shared__ __align__(128) unsigned char dsmem[];
     __shared__ int s_item, s_stage, s_plan;
@@ -703,7 +707,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             if ((wk & 255) > 1) {
                 const ExecArgs &aj = src.args(m);
                 pr.issue(aj, wk >> 8, wk & 255, lane);
-                ok = wait_deps(aj, pr, wk >> 8, wk & 255, src.epoch_of(m), lane);
+                ok = wait_deps<COUNT>(aj, pr, wk >> 8, wk & 255, src.epoch_of(m), lane);
             }
         }
         if (lane == 0) {
@@ -774,7 +778,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
                     const ExecArgs &an = src.args(mn);
                     pr.issue_range(an, lon, hin, wn & 255, lane);
                     ready = pr.fits() ? pr.ready(src.epoch_of(mn), lane)
-                                      : ready_wide(an, wn >> 8, wn & 255, src.epoch_of(mn), lane);
+                                      : ready_wide<COUNT>(an, wn >> 8, wn & 255, src.epoch_of(mn), lane);
                     if (ready) fence_acq_rel_gpu();
                 }
             }
@@ -782,11 +786,18 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             if (STAGED) consumed++;
             bool published = false;
             auto publish = [&]() {
-                if (published) return;
-                published = true;
+                if constexpr (COUNT) {   // a repeat store of the flag is harmless, a repeat count is not
+                    if (published) return;
+                    published = true;
+                }
                 const ExecArgs &aj = src.args(m);
                 const int32_t t = wk >> 8, k = wk & 255;
-                if (lane == 0 && !(t == aj.drop_tile && k == aj.drop_k)) publish_item(aj, t, k, src.epoch_of(m));
+                if (lane == 0 && !(t == aj.drop_tile && k == aj.drop_k)) {
+                    if constexpr (COUNT)
+                        publish_item(aj, t, k, src.epoch_of(m));
+                    else
+                        st_release_u32(aj.flags + (int64_t)k * aj.fstride + t, src.epoch_of(m));
+                }
             };
             if (jn >= g.n_items) {
                 publish();
@@ -797,7 +808,7 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
             }
             if (!ready) {   // publish first, then block on the next item's dependencies
                 publish();
-                ready = wait_deps(src.args(mn), pr, wn >> 8, wn & 255, src.epoch_of(mn), lane);
+                ready = wait_deps<COUNT>(src.args(mn), pr, wn >> 8, wn & 255, src.epoch_of(mn), lane);
             }
             if (ready && j + nst * G < g.n_items) issue(j + nst * G);   // the stage of item j is free
             if (lane == 0) {
@@ -826,9 +837,11 @@ __device__ __forceinline__ void wave_loop(const ExecArgs &g, const Src &src, con
         }
         done = __shfl_sync(0xffffffffu, done, 0);
         if (done == (int)gridDim.x - 1) {   // last CTA: clear the block counts, publish the epoch(s), reset
-            fence_acq_rel_gpu();
-            src.clear_counts(lane);
-            __syncwarp();
+            if constexpr (COUNT) {
+                fence_acq_rel_gpu();
+                src.clear_counts(lane);
+                __syncwarp();
+            }
             if (lane == 0) {
                 atomicExch(g.ctl + CTL_FINISHED, 0);
                 atomicExch(g.ctl + CTL_ABORT, 0);
@@ -1094,10 +1107,10 @@ __global__ void __launch_bounds__(kResThreads) k_res_wave(ExecArgs a) {
 // NW compute warps per CTA; with 16 of them a warp holds one chunk of a
 // 512-row item (more warps, fewer registers each: the FP64 form, whose
 // FP64 pipe wants more independent rows in flight), with 8 it holds two.
-template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED, int NW>
+template <typename VT, typename MT, int W, bool EXACT, bool DIAG, bool STAGED, int NW, bool COUNT>
 __global__ void MPK_WAVE_BOUNDS((NW + 1) * 32) k_wave(ExecArgs a) {
     const OnePlan src{a, (uint32_t)ld_relaxed_s32(a.ctl + CTL_EPOCH) + 1u};
-    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED, OnePlan, int, (NW >= 16 ? 1 : kPC)>(a, src, 0);
+    wave_loop<MpkNode<VT, MT, W, EXACT, DIAG>, MT, STAGED, OnePlan, int, (NW >= 16 ? 1 : kPC), COUNT>(a, src, 0);
 }
 
 // Baseline: one SpMV over all chunks (warp per chunk, grid-stride).
@@ -1739,15 +1752,21 @@ __global__ void k_permute(int32_t n, int32_t wpr, const int32_t *__restrict__ id
 }
 
 // ---------------------------------------------------------------- dispatch
-template <typename VT, typename MT, bool DIAG, bool STAGED, int NW = kComputeWarps>
-const void *wave_ptr(int nrhs) {
+template <typename VT, typename MT, bool DIAG, bool STAGED, int NW, bool COUNT>
+const void *wave_ptr_c(int nrhs) {
     switch (nrhs) {
-    case 1: return (const void *)k_wave<VT, MT, 1, true, DIAG, STAGED, NW>;
-    case 2: return (const void *)k_wave<VT, MT, 2, true, DIAG, STAGED, NW>;
-    case 4: return (const void *)k_wave<VT, MT, 4, true, DIAG, STAGED, NW>;
-    case 8: return (const void *)k_wave<VT, MT, 8, true, DIAG, STAGED, NW>;
-    default: return (const void *)k_wave<VT, MT, 8, false, DIAG, STAGED, NW>;
+    case 1: return (const void *)k_wave<VT, MT, 1, true, DIAG, STAGED, NW, COUNT>;
+    case 2: return (const void *)k_wave<VT, MT, 2, true, DIAG, STAGED, NW, COUNT>;
+    case 4: return (const void *)k_wave<VT, MT, 4, true, DIAG, STAGED, NW, COUNT>;
+    case 8: return (const void *)k_wave<VT, MT, 8, true, DIAG, STAGED, NW, COUNT>;
+    default: return (const void *)k_wave<VT, MT, 8, false, DIAG, STAGED, NW, COUNT>;
     }
+}
+// plans whose dependency ranges all fit a probe run the variant without counters
+template <typename VT, typename MT, bool DIAG, bool STAGED, int NW = kComputeWarps>
+const void *wave_ptr(const Plan *pl) {
+    return pl->wide_deps ? wave_ptr_c<VT, MT, DIAG, STAGED, NW, true>(pl->nrhs)
+                         : wave_ptr_c<VT, MT, DIAG, STAGED, NW, false>(pl->nrhs);
 }
 template <typename VT, typename MT, bool DIAG>
 const void *spmv_ptr(int nrhs) {
@@ -1762,8 +1781,8 @@ const void *spmv_ptr(int nrhs) {
 
 template <typename VT, typename MT, bool DIAG, int NW>
 const void *staged_wave_ptr(int nrhs) {   // the staged form runs block widths 1 and 2
-    return nrhs == 1 ? (const void *)k_wave<VT, MT, 1, true, DIAG, true, NW>
-                     : (const void *)k_wave<VT, MT, 2, true, DIAG, true, NW>;
+    return nrhs == 1 ? (const void *)k_wave<VT, MT, 1, true, DIAG, true, NW, true>
+                     : (const void *)k_wave<VT, MT, 2, true, DIAG, true, NW, true>;
 }
 template <bool STAGED>
 const void *pick_wave_t(const Plan *pl) {
@@ -1773,10 +1792,10 @@ const void *pick_wave_t(const Plan *pl) {
         if (pl->val_bytes == 2) return staged_wave_ptr<float, __nv_bfloat16, true, kFp32Warps>(pl->nrhs);
         return staged_wave_ptr<float, float, true, kFp32Warps>(pl->nrhs);
     } else {
-        if (pl->prec == MPK_F64) return wave_ptr<double, double, false, false, kFp64Warps>(pl->nrhs);
-        if (!pl->has_diag) return wave_ptr<float, float, false, false, kFp32Warps>(pl->nrhs);
-        if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, false, kFp32Warps>(pl->nrhs);
-        return wave_ptr<float, float, true, false, kFp32Warps>(pl->nrhs);
+        if (pl->prec == MPK_F64) return wave_ptr<double, double, false, false, kFp64Warps>(pl);
+        if (!pl->has_diag) return wave_ptr<float, float, false, false, kFp32Warps>(pl);
+        if (pl->val_bytes == 2) return wave_ptr<float, __nv_bfloat16, true, false, kFp32Warps>(pl);
+        return wave_ptr<float, float, true, false, kFp32Warps>(pl);
     }
 }
 template <bool STAGED, int G>
