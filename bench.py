@@ -42,6 +42,9 @@ CONFIGS = {
     "laplace3d-160-p8-f64df": ("laplace3d", 160, 8, "f64df",
                                "3D 7-point Laplacian 160^3, p=8, FP64 inputs and outputs, double-float arithmetic "
                                "on the FP32 pipe"),
+    "laplace3d-160-p8-bf16val": ("laplace3d", 160, 8, "bf16val",
+                                 "3D 7-point Laplacian 160^3, p=8, FP32 vectors and accumulation, the BF16-exact "
+                                 "off-diagonal values (-1) in BF16 and the diagonal (6) in FP32"),
     "laplace2d-64-p4-f64": ("laplace2d", 64, 4, "f64", "2D 5-point Laplacian 64^2, p=4, FP64"),
     "anderson200-cheb64-p8-bf16val": ("anderson3d", 200, 8, "bf16val",
                                       "3D Anderson 200^3 periodic (W=16.5), Chebyshev degree 64 in sweeps of "
@@ -94,9 +97,12 @@ def cheb_config(desc, A, p, prec):
 
 def one_read_bytes(nnz, n, p, prec, nrhs=1):
     """Algorithmic bytes of one MPK (the one-matrix-read lower bound): the
-    packed matrix once (value + 32-bit column per entry), the row pointers,
-    x and the p outputs."""
+    packed matrix once (value + 32-bit column per entry; with BF16 values, 2
+    bytes per off-diagonal value and the FP32 diagonal apart), the row
+    pointers, x and the p outputs."""
     vb = vec_bytes(prec)
+    if prec == "bf16val":
+        return (nnz - n) * (2 + 4) + 4 * n + 4 * (n + 1) + vb * n * nrhs * (1 + p)
     return nnz * (vb + 4) + 4 * (n + 1) + vb * n * nrhs * (1 + p)
 
 
@@ -507,8 +513,9 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"f64": "f64", "f32": "f32", "f64df": "f32x2"}[prec],
+        "dtype": {"f64": "f64", "f32": "f32", "f64df": "f32x2", "bf16val": "f32"}[prec],
         "arithmetic": {"f64": "FP64", "f32": "FP32",
+                       "bf16val": "FP32 (BF16-exact off-diagonal values widened to FP32, FP32 diagonal)",
                        "f64df": "double-float (pairs of FP32, compensated row sums) on the FP32 pipe; FP64 x and Y, "
                                 "every output rounded once to FP64"}[prec],
         "data": "synthetic",
