@@ -510,7 +510,7 @@ int mpk_plan_debug_drop_flag(mpk_plan_t plan, int32_t tile, int32_t power);
  * use this call.
  *
  * The scratch (frontier queue and control words) is a static device array
- * inside this library, sized for n <= 1,048,576 vertices (about 8 MB, held
+ * inside this library, sized for n <= 1,048,576 vertices (about 4 MB, held
  * on every GPU that loads the library until the process exits).  The caller
  * passes the inputs and the output: n, nnz and the CRS arrays rowptr[n+1],
  * col[nnz] (DEVICE, caller-owned; the stored pattern is taken as symmetric),

@@ -40,15 +40,20 @@ void free_batch(Batch *b) {
 // power, the CTAs hold items of the others.  (Plans one after another, the
 // largest first, measured 213 vs 209 ms on the 64-matrix Zipf batch and
 // 322 vs 287 ms with the default options.)
-void merge_orders(const std::vector<Plan *> &plans, std::vector<int32_t> &work, std::vector<int32_t> &wplan) {
+int merge_orders(const std::vector<Plan *> &plans, std::vector<int32_t> &work, std::vector<int32_t> &wplan) {
+    std::vector<std::vector<int32_t>> own(plans.size());
+    for (size_t m = 0; m < plans.size(); m++) {
+        const int rc = work_to_host(plans[m], own[m]);
+        if (rc != MPK_OK) return rc;
+    }
     struct Ref { double pos; int32_t m, j; };
     std::vector<Ref> refs;
     size_t total = 0;
-    for (const Plan *pl : plans) total += pl->h_work.size();
+    for (const auto &w : own) total += w.size();
     refs.reserve(total);
     for (int32_t m = 0; m < (int32_t)plans.size(); m++) {
-        const double n = (double)plans[m]->h_work.size();
-        for (int32_t j = 0; j < (int32_t)plans[m]->h_work.size(); j++) refs.push_back({(j + 0.5) / n, m, j});
+        const double n = (double)own[m].size();
+        for (int32_t j = 0; j < (int32_t)own[m].size(); j++) refs.push_back({(j + 0.5) / n, m, j});
     }
     std::sort(refs.begin(), refs.end(), [](const Ref &a, const Ref &b) {
         return a.pos != b.pos ? a.pos < b.pos : (a.m != b.m ? a.m < b.m : a.j < b.j);
@@ -56,9 +61,10 @@ void merge_orders(const std::vector<Plan *> &plans, std::vector<int32_t> &work, 
     work.resize(total);
     wplan.resize(total);
     for (size_t i = 0; i < total; i++) {
-        work[i] = plans[refs[i].m]->h_work[refs[i].j];
+        work[i] = own[refs[i].m][refs[i].j];
         wplan[i] = refs[i].m;
     }
+    return MPK_OK;
 }
 
 int upload_table(Batch *b, const void *const *xs, void *const *Ys, cudaStream_t st) {
@@ -105,7 +111,7 @@ int build_batch(Batch *b, const mpk_plan_t *plans, int32_t count) {
     b->prec = b->plans[0]->prec;
     b->stream = b->plans[0]->stream;
     std::vector<int32_t> work, wplan;
-    merge_orders(b->plans, work, wplan);
+    MPK_TRYB(merge_orders(b->plans, work, wplan));
     b->n_items = (int32_t)work.size();
     MPK_TRYB(dev_alloc<int32_t>(nullptr, &b->d_work, work.size()));
     MPK_TRYB(dev_alloc<int32_t>(nullptr, &b->d_wplan, wplan.size()));

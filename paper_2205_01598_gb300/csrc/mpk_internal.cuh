@@ -85,7 +85,7 @@ struct Plan {
     int64_t stage_entries = 0;      // capacity of one stage in packed entries
     size_t smem_bytes = 0;          // dynamic shared memory per wavefront CTA
     // host copies kept to build the issue order of shorter sweeps
-    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_lo, h_dep_hi, h_work;
+    std::vector<int32_t> h_tile_row, h_group_tile, h_dep_lo, h_dep_hi;
     int32_t *d_work_rem = nullptr;  // issue order for rem_p powers (Chebyshev remainder sweep)
     int32_t rem_p = 0;
 
@@ -227,6 +227,11 @@ ExecArgs exec_args(const Plan *pl, const void *x, void *Y);
 int ensure_io(Plan *pl, size_t bytes);
 // Issue order of the (tile, power) items for powers 1..p_sweep (mpk_plan.cu).
 double order_items(const Plan *pl, int32_t p_sweep, double lag, std::vector<int32_t> &work);
+// Tile positions v(t) in level-group units and the slope of that order (lag
+// resolved in place when negative).
+double order_slope(const Plan *pl, int32_t p, double &lag, std::vector<double> &v);
+// The plan's issue order (d_work), copied to the host (synchronises the plan's stream).
+int work_to_host(const Plan *pl, std::vector<int32_t> &work);
 int wave_occupancy(const Plan *pl, int *wave_ctas, int *cheb_ctas);
 const void *batch_kernel(int prec);
 int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t st, int threads = kWaveThreads);

@@ -197,41 +197,26 @@ __device__ bool grid_sync(BfsCtl *c, uint32_t &b, uint64_t timeout_ns) {
     return s_ok != 0;
 }
 
-// Frontier entries hold the row range of their vertex, {first entry, length}
-// in the pattern (q) and in its transpose (tq, when there is one), written by
-// the lane that claimed the vertex: expanding an entry then starts at its
-// columns, without a lookup of the row pointers.
-__device__ __forceinline__ void bfs_put(int64_t pos, int32_t v, const int32_t *__restrict__ rp,
-                                        const int32_t *__restrict__ trp, int2 *q, int2 *tq) {
-    const int32_t a = __ldg(rp + v);
-    q[pos] = make_int2(a, __ldg(rp + v + 1) - a);
-    if (trp) {
-        const int32_t t = __ldg(trp + v);
-        tq[pos] = make_int2(t, __ldg(trp + v + 1) - t);
-    }
-}
-
-// Expands the frontier q[start, end) of level L: warps warp0, warp0 + nwarps,
-// ... take 32 frontier entries each; a lane loads up to kBfsBatch neighbours,
-// then tests them, then claims the unvisited ones with a compare-and-swap
-// (so the loads of a batch overlap), and the warp appends its claims after
-// end with one atomic add.
+// Expands the frontier queue[start, end) of level L: warps warp0,
+// warp0 + nwarps, ... take 32 frontier vertices each; a lane loads up to
+// kBfsBatch neighbours, then tests them, then claims the unvisited ones with
+// a compare-and-swap (so the loads of a batch overlap), and the warp appends
+// its claims to the queue after end with one atomic add.
 __device__ __forceinline__ void bfs_expand(int64_t start, int64_t end, int64_t warp0, int64_t nwarps, int lane,
                                            const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                            const int32_t *__restrict__ trp, const int32_t *__restrict__ tcol,
-                                           int32_t L, int32_t *level, int2 *q, int2 *tq, int *next_cnt) {
+                                           int32_t L, int32_t *level, int32_t *queue, int *next_cnt) {
     for (int64_t base = start + warp0 * 32; base < end; base += nwarps * 32) {
         const int64_t i = base + lane;
         const bool valid = i < end;
         int32_t a0 = 0, da = 0, t0 = 0, dt = 0;
         if (valid) {
-            const int2 e = q[i];
-            a0 = e.x;
-            da = e.y;
+            const int32_t u = queue[i];
+            a0 = __ldg(rp + u);
+            da = __ldg(rp + u + 1) - a0;
             if (trp) {
-                const int2 te = tq[i];
-                t0 = te.x;
-                dt = te.y;
+                t0 = __ldg(trp + u);
+                dt = __ldg(trp + u + 1) - t0;
             }
         }
         const int32_t deg = da + dt;
@@ -243,9 +228,6 @@ __device__ __forceinline__ void bfs_expand(int64_t start, int64_t end, int64_t w
                 const int32_t j = j0 + b;
                 v[b] = j < deg ? (j < da ? __ldg(col + a0 + j) : __ldg(tcol + t0 + (j - da))) : -1;
             }
-            // a relaxed load first: most neighbours are already claimed, and a
-            // compare-and-swap on every one of them queues on the hubs of
-            // skewed graphs (measured: Zipf N = 2M 1.85 vs 1.41 ms without it)
             unsigned disc = 0;
 #pragma unroll
             for (int b = 0; b < kBfsBatch; b++)
@@ -268,7 +250,7 @@ __device__ __forceinline__ void bfs_expand(int64_t start, int64_t end, int64_t w
             int64_t pos = end + at + (incl - mine);
 #pragma unroll
             for (int b = 0; b < kBfsBatch; b++)
-                if ((disc >> b) & 1u) bfs_put(pos++, v[b], rp, trp, q, tq);
+                if ((disc >> b) & 1u) queue[pos++] = v[b];
         }
     }
 }
@@ -289,8 +271,7 @@ __device__ __forceinline__ void bfs_expand(int64_t start, int64_t end, int64_t w
 // round's slots.
 __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *rp, const int32_t *col,
                                                      const int32_t *trp, const int32_t *tcol, int32_t root,
-                                                     int32_t *level, int2 *q, int2 *tq, BfsCtl *c,
-                                                     uint64_t timeout_ns) {
+                                                     int32_t *level, int32_t *queue, BfsCtl *c, uint64_t timeout_ns) {
     __shared__ int s_cnt[3];
     const int lane = threadIdx.x & 31;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,7 +279,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
     const int64_t gwarp = gtid >> 5, nwarps = gsize >> 5;
     if (gtid == 0) {
         level[root] = 0;
-        bfs_put(0, root, rp, trp, q, tq);
+        queue[0] = root;
         c->cnt[1] = 1;   // read after the first barrier (round 1)
         c->cnt[2] = 0;
         c->found[0] = c->found[1] = c->found[2] = INT_MAX;
@@ -330,7 +311,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
             cursor = f + 1;
             if (gtid == 0) {
                 level[f] = L;
-                bfs_put(start, f, rp, trp, q, tq);
+                queue[start] = f;
                 atomicExch(&c->cnt[(R + 1) % 3], 1);
                 atomicExch(&c->cnt[(R + 2) % 3], 0);
             }
@@ -351,7 +332,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
                     // previous __syncthreads)
                     if (threadIdx.x == 0) s_cnt[(run + 1) % 3] = 0;
                     const int64_t e = s0 + sz;
-                    bfs_expand(s0, e, threadIdx.x >> 5, blockDim.x >> 5, lane, rp, col, trp, tcol, l, level, q, tq,
+                    bfs_expand(s0, e, threadIdx.x >> 5, blockDim.x >> 5, lane, rp, col, trp, tcol, l, level, queue,
                                &s_cnt[run % 3]);
                     __syncthreads();
                     s0 = e;
@@ -373,7 +354,7 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
             continue;
         }
         if (gtid == 0) atomicExch(&c->cnt[(R + 2) % 3], 0);
-        bfs_expand(start, start + size, gwarp, nwarps, lane, rp, col, trp, tcol, L, level, q, tq,
+        bfs_expand(start, start + size, gwarp, nwarps, lane, rp, col, trp, tcol, L, level, queue,
                    &c->cnt[(R + 1) % 3]);
         if (!grid_sync(c, nbar, timeout_ns)) return;
         R++;
@@ -384,18 +365,48 @@ __global__ void __launch_bounds__(kBfsThreads) k_bfs(int32_t n, const int32_t *r
 }
 
 // Cooperative launch of k_bfs: one CTA per SM.
-// The frontier queue holds n int2 entries (2n ints), and as many more for
-// the transposed pattern when trp is given.
 int launch_bfs(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *trp, const int32_t *tcol, int32_t root,
                int32_t *level, int32_t *queue, BfsCtl *c, uint64_t timeout_ns, int num_sms, cudaStream_t st) {
     int occ = 0;
     MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bfs, kBfsThreads, 0));
     if (occ < 1) return MPK_ERR_CUDA;
-    int2 *q = (int2 *)queue, *tq = trp ? q + n : nullptr;
     void *args[] = {(void *)&n, (void *)&rp, (void *)&col, (void *)&trp, (void *)&tcol, (void *)&root,
-                    (void *)&level, (void *)&q, (void *)&tq, (void *)&c, (void *)&timeout_ns};
+                    (void *)&level, (void *)&queue, (void *)&c, (void *)&timeout_ns};
     MPK_CUDA(cudaLaunchCooperativeKernel((void *)k_bfs, dim3(num_sms), dim3(kBfsThreads), args, 0, st));
     return MPK_OK;
+}
+
+// ---------------------------------------------------------------- issue order on the GPU
+// The order of order_items for a plan without recursion, one thread per
+// item: item (t, k) of sweep s (powers k0..k1) goes to position s*q*T plus,
+// over the sweep's powers k', the number of items (t', k') that sort before
+// it by (key, k, t), key(t, k) = v(t) + sigma * (k - k0).  Keys of one power
+// do not decrease with t, so each count is a binary search (for k' = k it is
+// t itself); the keys are rounded as the host rounds them (no contraction).
+__global__ void k_issue_order(int32_t T, int32_t p, int32_t q, double sigma, const double *__restrict__ v,
+                              int32_t *work) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)T * p) return;
+    const int32_t k = (int32_t)(id / T) + 1, t = (int32_t)(id % T);
+    const int32_t s = (k - 1) / q, k0 = s * q + 1, k1 = min(p, k0 + q - 1);
+    const double key = __dadd_rn(__ldg(v + t), __dmul_rn(sigma, (double)(k - k0)));
+    int64_t pos = (int64_t)s * q * T;
+    for (int32_t kk = k0; kk <= k1; kk++) {
+        if (kk == k) {
+            pos += t;
+            continue;
+        }
+        const double sh = __dmul_rn(sigma, (double)(kk - k0));
+        int32_t lo = 0, hi = T;   // first t' that sorts after (t, k)
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            const double km = __dadd_rn(__ldg(v + mid), sh);
+            if (kk < k ? km <= key : km < key) lo = mid + 1;
+            else hi = mid;
+        }
+        pos += lo;
+    }
+    work[pos] = (t << 8) | k;
 }
 
 // ---------------------------------------------------------------- stable radix sort by level
@@ -923,7 +934,7 @@ static int refine_levels(Plan *pl, const mpk_csr *A, int32_t p, int32_t s_max, d
     MPK_TRY(S.alloc(&srow, (size_t)n + 1));
     MPK_TRY(S.alloc(&scol, (size_t)std::max<int64_t>(1, A->nnz)));
     MPK_TRY(S.alloc(&slev, (size_t)n));
-    MPK_TRY(S.alloc(&queue, 2 * (size_t)n));
+    MPK_TRY(S.alloc(&queue, (size_t)n));
     MPK_TRY(S.alloc(&perm2, (size_t)n));
     MPK_TRY(S.alloc(&d_meta, 2 * (size_t)n + 2));
     MPK_TRY(S.alloc(&d_lp, (size_t)n + 1));
@@ -1106,7 +1117,7 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     int32_t *d_queue;
     BfsCtl *d_bc;
     MPK_TRY(dev_alloc(pl, &pl->d_level, (size_t)n));
-    MPK_TRY(S.alloc(&d_queue, (A->assume_symmetric ? 2 : 4) * (size_t)n));
+    MPK_TRY(S.alloc(&d_queue, (size_t)n));
     MPK_TRY(S.alloc(&d_bc, 1));
     MPK_CUDA(cudaMemsetAsync(pl->d_level, 0xff, sizeof(int32_t) * (size_t)n, st));
     MPK_CUDA(cudaMemsetAsync(d_bc, 0, sizeof(BfsCtl), st));
@@ -1510,13 +1521,28 @@ int build_plan(Plan *pl, const mpk_csr *A, int32_t p, const mpk_opts *o) {
     {
         pl->h_tile_row = tile_row;
         pl->h_group_tile = group_tile;
-        std::vector<int32_t> work;
         pl->lag = o->lag;
-        pl->slope = order_items(pl, p, o->lag, work);
-        MPK_TRY(dev_alloc(pl, &pl->d_work, work.size()));
-        MPK_CUDA(cudaMemcpyAsync(pl->d_work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
+        const size_t items = (size_t)pl->n_tiles * p;
+        MPK_TRY(dev_alloc(pl, &pl->d_work, items));
+        if (pl->rec_stages == 0) {
+            // without recursion the order is a merge of shifted copies of one
+            // sorted list: placed on the GPU (k_issue_order)
+            double lag = o->lag;
+            std::vector<double> v;
+            pl->slope = order_slope(pl, p, lag, v);
+            double *d_v;
+            MPK_TRY(S.alloc(&d_v, v.size()));
+            MPK_CUDA(cudaMemcpyAsync(d_v, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, st));
+            const int32_t q = pl->sweep > 0 ? std::min(pl->sweep, p) : p;
+            k_issue_order<<<blocks_for((int64_t)items, 256), 256, 0, st>>>(pl->n_tiles, p, q, pl->slope, d_v,
+                                                                          pl->d_work);
+            MPK_CUDA(cudaGetLastError());
+        } else {
+            std::vector<int32_t> work;
+            pl->slope = order_items(pl, p, o->lag, work);
+            MPK_CUDA(cudaMemcpyAsync(pl->d_work, work.data(), work.size() * 4, cudaMemcpyHostToDevice, st));
+        }
         MPK_CUDA(cudaStreamSynchronize(st));
-        pl->h_work = std::move(work);
     }
     mark(6);
     pl->fstride = ((pl->n_tiles + 3) / 4) * 4 + 4;
@@ -1545,7 +1571,7 @@ static_assert(sizeof(BfsCtl) <= kStaticBadWord * sizeof(int32_t), "control block
 
 }  // namespace
 
-static __device__ __align__(256) int32_t g_levels_scratch[kStaticCtlWords + 2 * kStaticLevelsMaxN];
+static __device__ __align__(256) int32_t g_levels_scratch[kStaticCtlWords + kStaticLevelsMaxN];
 
 namespace {
 
@@ -1582,11 +1608,13 @@ int static_levels_scratch(int32_t **out) {
 // With sweeps of q < p powers (Sec. 5.1 splits a power into sweeps) the
 // powers of sweep s = (k-1) / q come after every item of sweep s-1, each
 // sweep traversed as above with k - 1 replaced by its power within the sweep.
-double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &work) {
+// Tile positions v(t) in level-group units and the slope sigma of the
+// issue order below (its lag resolved), for p powers in sweeps of q.
+double order_slope(const Plan *pl, int32_t p, double &lag, std::vector<double> &v) {
     const std::vector<int32_t> &tile_row = pl->h_tile_row, &group_tile = pl->h_group_tile, &hi = pl->h_dep_hi;
     const int32_t T = pl->n_tiles, G = pl->n_groups;
     const int32_t q = pl->sweep > 0 ? std::min(pl->sweep, p) : p;
-    std::vector<double> v((size_t)T);
+    v.assign((size_t)T, 0.0);
     for (int32_t g = 0; g < G; g++) {
         const double r0 = tile_row[group_tile[g]], r1 = tile_row[group_tile[g + 1]];
         for (int32_t t = group_tile[g]; t < group_tile[g + 1]; t++) v[t] = g + (tile_row[t] - r0) / (r1 - r0);
@@ -1600,7 +1628,15 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
         const int32_t grid = pl->cheb_grid > 0 ? std::min(pl->grid_ctas, pl->cheb_grid) : pl->grid_ctas;
         lag = 1.5 * (double)grid / ((double)q * tiles_per_group);
     }
-    const double sigma = std::max(1.0, need + lag);
+    return std::max(1.0, need + lag);
+}
+
+double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &work) {
+    const std::vector<int32_t> &hi = pl->h_dep_hi;
+    const int32_t T = pl->n_tiles;
+    const int32_t q = pl->sweep > 0 ? std::min(pl->sweep, p) : p;
+    std::vector<double> v;
+    const double sigma = order_slope(pl, p, lag, v);
     struct Item { int32_t s; double key; int32_t k, t; };
     std::vector<Item> items;
     items.reserve((size_t)T * p);
@@ -1694,6 +1730,14 @@ double order_items(const Plan *pl, int32_t p, double lag, std::vector<int32_t> &
     work.resize(items.size());
     for (size_t i = 0; i < items.size(); i++) work[i] = (items[i].t << 8) | items[i].k;
     return slope;
+}
+
+int work_to_host(const Plan *pl, std::vector<int32_t> &work) {
+    work.resize((size_t)pl->n_tiles * pl->p);
+    MPK_CUDA(cudaMemcpyAsync(work.data(), pl->d_work, sizeof(int32_t) * work.size(), cudaMemcpyDeviceToHost,
+                             pl->stream));
+    MPK_CUDA(cudaStreamSynchronize(pl->stream));
+    return MPK_OK;
 }
 
 int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t st, int32_t *total) {
