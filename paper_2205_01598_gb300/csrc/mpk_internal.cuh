@@ -239,7 +239,10 @@ int launch_coop(const void *fn, int grid, size_t smem, void **args, cudaStream_t
 inline bool is_f64_vec(int prec) { return prec == MPK_F64 || prec == MPK_F64_DF; }
 inline int elem_bytes_of(const Plan *pl) { return is_f64_vec(pl->prec) ? 8 : 4; }
 inline int wave_threads(const Plan *pl) { return pl->resident ? kResThreads : (pl->wave_warps + 1) * 32; }
-inline int cheb_threads(const Plan *pl) { return pl->resident ? kResThreads : kWaveThreads; }
+inline int cheb_threads(const Plan *pl) {
+    if (pl->resident) return kResThreads;
+    return pl->prec == MPK_F64 && pl->nrhs == 1 ? (kFp64Warps + 1) * 32 : kWaveThreads;   // see k_cheb_wave
+}
 
 }  // namespace mpk
 
