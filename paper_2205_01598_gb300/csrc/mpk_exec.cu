@@ -1417,13 +1417,20 @@ struct ChebNode {
     }
 };
 
-// NW compute warps; the real FP64 propagation runs 16 of them holding one
-// chunk each at two CTAs per SM (as the FP64 MPK: more rows in flight for the
-// FP64 pipe), the others 8 holding two.
-template <typename VT, typename MT, bool DIAG, bool STAGED, int G, bool MULTI, int NW = kComputeWarps>
-__global__ void __launch_bounds__((NW + 1) * 32, (NW >= 16 ? 2 : 1)) k_cheb_wave(ChebArgs ca) {
+template <typename VT, typename MT, bool DIAG, bool STAGED, int G, bool MULTI>
+__global__ void __launch_bounds__(kWaveThreads) k_cheb_wave(ChebArgs ca) {
     const OnePlan src{ca.e, (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u};
-    wave_loop<ChebNode<VT, MT, DIAG, G, MULTI>, MT, STAGED, OnePlan, ChebArgs, (NW >= 16 ? 1 : kPC)>(ca.e, src, ca);
+    wave_loop<ChebNode<VT, MT, DIAG, G, MULTI>, MT, STAGED>(ca.e, src, ca);
+}
+// The real FP64 propagation: 16 compute warps holding one chunk each at two
+// CTAs per SM, as the FP64 MPK (more rows in flight for the FP64 pipe).  (A
+// minimum of blocks in the bounds of the 8-warp kernel above changes its
+// register allocation: the Anderson propagation went from 72 to 96 registers
+// and 9.4 to 22.5 ms.)
+template <bool STAGED, bool MULTI>
+__global__ void __launch_bounds__((kFp64Warps + 1) * 32, 2) k_cheb_wave_f64r(ChebArgs ca) {
+    const OnePlan src{ca.e, (uint32_t)ld_relaxed_s32(ca.e.ctl + CTL_EPOCH) + 1u};
+    wave_loop<ChebNode<double, double, false, 1, MULTI>, double, STAGED, OnePlan, ChebArgs, 1>(ca.e, src, ca);
 }
 
 // Two CTAs per SM must fit (the resident schedule's grid may use them).
@@ -1805,13 +1812,15 @@ template <bool STAGED, int G>
 const void *pick_cheb_g(const Plan *pl, bool multi) {
     if (multi) {
         if (pl->prec == MPK_F64)
-            return (const void *)k_cheb_wave<double, double, false, STAGED, G, true, (G == 1 ? kFp64Warps : kComputeWarps)>;
+            return G == 1 ? (const void *)k_cheb_wave_f64r<STAGED, true>
+                          : (const void *)k_cheb_wave<double, double, false, STAGED, G, true>;
         if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED, G, true>;
         if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED, G, true>;
         return (const void *)k_cheb_wave<float, float, true, STAGED, G, true>;
     }
     if (pl->prec == MPK_F64)
-        return (const void *)k_cheb_wave<double, double, false, STAGED, G, false, (G == 1 ? kFp64Warps : kComputeWarps)>;
+        return G == 1 ? (const void *)k_cheb_wave_f64r<STAGED, false>
+                      : (const void *)k_cheb_wave<double, double, false, STAGED, G, false>;
     if (!pl->has_diag) return (const void *)k_cheb_wave<float, float, false, STAGED, G, false>;
     if (pl->val_bytes == 2) return (const void *)k_cheb_wave<float, __nv_bfloat16, true, STAGED, G, false>;
     return (const void *)k_cheb_wave<float, float, true, STAGED, G, false>;
