@@ -96,3 +96,37 @@ def test_sweeps_in_one_launch_are_ordered_by_sweep(name, p, q):
     gp = mpk.mpk_plan_perm(plan)[2].cpu().numpy()
     gq = mpk.mpk_plan_perm(plan_of(A, q, prec="f64", **kw))[2].cpu().numpy()
     assert np.array_equal(gp, gq)
+
+
+@pytest.mark.parametrize("name", ["laplace3d-30", "laplace3d-30-tiny-tiles", "zipf-8000", "box27-12", "diag-500"])
+@pytest.mark.parametrize("p,q", [(8, 8), (8, 3), (5, 1)])
+def test_issue_order_is_the_sorted_wavefront(name, p, q):
+    """The plan's issue order (placed on the GPU) is exactly the sort of the
+    items by (key, k, t) within each sweep, key = v(t) + slope * (k - k0):
+    v(t) = group index + the fraction of the group's rows before tile t, the
+    slope as the plan reports it, k0 the sweep's first power."""
+    make, kw = CASES[name]
+    A = make()
+    plan = plan_of(A, p, prec="f64", sweep=q, **kw)
+    info = mpk.mpk_plan_info(plan)
+    assert info["rec_stages"] == 0
+    _, lp, gp, _ = (t.cpu().numpy() for t in mpk.mpk_plan_perm(plan))
+    work, _, _ = mpk.mpk_plan_schedule(plan)
+    tr = info["tile_rows"]
+    v, T = [], 0
+    for g in range(len(gp) - 1):
+        r0, r1 = int(lp[gp[g]]), int(lp[gp[g + 1]])
+        for a in range(r0, r1, tr):
+            v.append(g + float(a - r0) / float(r1 - r0))
+    T = len(v)
+    assert T == info["n_tiles"]
+    sigma = info["slope"]
+    items = []
+    for k in range(1, p + 1):
+        s = (k - 1) // q
+        k0 = s * q + 1
+        for t in range(T):
+            items.append((s, v[t] + sigma * (k - k0), k, t))
+    items.sort()
+    want = np.array([(t << 8) | k for _, _, k, t in items], dtype=np.int32)
+    assert np.array_equal(work, want)
